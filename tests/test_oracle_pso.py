@@ -1,0 +1,103 @@
+"""Pins for the oracle's particle swarm (Algorithm 1 steps 3-9) and driver."""
+import numpy as np
+import pytest
+
+from oracle import pso
+from paper_2002_01981_gb300 import phantoms
+
+
+def _bowl(xy, target=(0.3, 0.7)):
+    return (xy[:, 0] - target[0]) ** 2 + (xy[:, 1] - target[1]) ** 2
+
+
+def test_swarm_reaches_bowl_minimum():
+    s = pso.Swarm(16, seed=11)
+    f0 = _bowl(s.x).min()
+    for _ in range(80):
+        pso.pso_step(s, _bowl(s.x))
+    b = pso.best_particle(s)
+    # no inertia weight (Alg 1 step 7): the swarm stalls near, not at, the minimum
+    assert np.allclose(s.pbest_x[b], [0.3, 0.7], atol=1e-2)
+    assert s.pbest_f[b] < 1e-4 and s.pbest_f[b] < f0 / 10
+
+
+def test_minimum_on_the_box_edge_is_reached():
+    # the target lies outside [0,1]^2: the clipped swarm must sit on the edge
+    s = pso.Swarm(12, seed=3)
+    for _ in range(60):
+        pso.pso_step(s, _bowl(s.x, (1.4, -0.2)))
+    b = pso.best_particle(s)
+    assert np.allclose(s.pbest_x[b], [1.0, 0.0], atol=1e-6)
+
+
+def test_positions_and_velocities_stay_bounded():
+    s = pso.Swarm(9, seed=5, vmax=0.15)
+    rng = np.random.default_rng(0)
+    assert np.all(np.abs(s.v) <= 0.15) and np.all((s.x >= 0) & (s.x < 1))
+    for _ in range(30):
+        pso.pso_step(s, rng.random(9))
+        assert np.all(np.abs(s.v) <= 0.15)
+        assert np.all((s.x >= 0) & (s.x <= 1))
+
+
+def test_lbest_ring_by_hand():
+    f = np.array([5.0, 1.0, 7.0, 7.0, 0.5, 9.0])
+    # rings (radius 1, wrapping): {5,0,1},{0,1,2},{1,2,3},{2,3,4},{3,4,5},{4,5,0}
+    assert list(pso.lbest_index(f)) == [1, 1, 1, 4, 4, 4]
+    g = np.array([2.0, 2.0, 2.0, 2.0])          # ties go to the lowest index
+    assert list(pso.lbest_index(g)) == [0, 0, 1, 0]
+    assert list(pso.lbest_index(np.array([3.0]))) == [0]
+    assert list(pso.lbest_index(f, radius=2)) == [4, 1, 4, 4, 4, 4]
+
+
+def test_pbest_needs_strict_improvement():
+    s = pso.Swarm(3, seed=2)
+    pso.pso_step(s, np.array([1.0, 2.0, 3.0]))
+    keep = s.pbest_x.copy()
+    pso.pso_step(s, np.array([1.0, 2.0, 3.0]))    # equal fitness: no update
+    assert np.array_equal(s.pbest_x, keep)
+    x_now = s.x.copy()
+    pso.pso_step(s, np.array([0.5, 2.0, np.nan]))  # strict improvement / NaN
+    assert np.array_equal(s.pbest_x[0], x_now[0])
+    assert np.array_equal(s.pbest_x[2], keep[2]) and s.pbest_f[2] == 3.0
+
+
+def test_zero_attraction_keeps_velocity():
+    # with x = pbest = lbest the update is v <- v (clamped), x <- x + v
+    s = pso.Swarm(4, seed=9)
+    s.pbest_f = np.full(4, -np.inf)      # nothing can improve
+    s.pbest_x = s.x.copy()
+    s.pbest_x[:] = s.x
+    s.pbest_x = np.tile(s.x[:1], (4, 1))
+    s.x = s.pbest_x.copy()
+    v0, x0 = s.v.copy(), s.x.copy()
+    pso.pso_step(s, np.zeros(4))
+    assert np.array_equal(s.v, v0)
+    assert np.array_equal(s.x, np.clip(x0 + v0, 0, 1))
+
+
+def test_resume_is_bit_identical():
+    rng = np.random.default_rng(1)
+    fits = [rng.random(7) for _ in range(10)]
+    a = pso.Swarm(7, seed=42)
+    for f in fits:
+        pso.pso_step(a, f)
+    b = pso.Swarm(7, seed=42)
+    for f in fits[:4]:
+        pso.pso_step(b, f)
+    saved = b.copy()
+    for f in fits[4:]:
+        pso.pso_step(saved, f)
+    assert np.array_equal(a.x, saved.x) and np.array_equal(a.v, saved.v)
+    assert np.array_equal(a.pbest_f, saved.pbest_f) and a.gen == saved.gen == 10
+
+
+@pytest.mark.slow
+def test_pifcm3d_small_end_to_end():
+    vol = phantoms.ellipse_slice(16, seed=1, sigma=0.05)
+    out = pso.pifcm3d(vol, c=4, P=4, generations=3, seed=1, max_iter=10)
+    U, C = out["U"], out["C"]
+    assert np.allclose(U.sum(axis=0), 1.0, atol=1e-13)
+    assert np.all(np.diff(np.sort(C)) > 0.1)          # four distinct grey levels
+    assert 0 <= out["lambda"] <= 1 and 0 <= out["xi"] <= 1
+    assert out["J"] <= out["pbest_f"].min() * (1 + 1e-12) + 1e-15
