@@ -1,0 +1,230 @@
+/*
+ * pifcm.h - C ABI of the GB300 (sm_103a) implementation of the 3DPIFCM hot path.
+ *
+ * 3DPIFCM (Agranonik, Herman, Last, "Parallel 3DPIFCM Algorithm for Noisy Brain
+ * MRI Images", arXiv 2002.01981) is fuzzy C-means whose distance carries two
+ * neighbourhood terms weighted by (lambda, xi) (Eqs 1-10), with (lambda, xi)
+ * chosen by a particle swarm whose fitness is the objective J_m (Algorithm 1).
+ * This library runs the whole path on one GPU: min-max normalisation
+ * (Algorithm 2 step 1), the FCM start (Algorithm 1 step 2), the batched fitness
+ * evaluation of all particles (Algorithm 1 step 4: one IFCM run per particle),
+ * the swarm update (steps 5-8) and the final IFCM run at the best particle
+ * (step 11).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Volumes are float32 arrays [nz][ny][pitch_x], x fastest; elements with
+ *   x >= nx are padding and are never read.  A 2D image is nz = 1.  pitch_x
+ *   must be >= nx and a multiple of 4 (16-byte rows); base pointers must be
+ *   16-byte aligned.
+ * - Memberships are float32 arrays [c][nz][ny][pitch_x] (one plane per
+ *   cluster); padding elements of outputs are unspecified.
+ * - "device" pointers are CUDA device memory owned by the caller; "host"
+ *   pointers are ordinary host memory owned by the caller.  The library never
+ *   allocates: its only scratch is the caller's workspace `ws` of at least the
+ *   size the matching *_workspace_bytes() call returns (256-byte aligned).
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *   stream-ordered and return without synchronising, except the *_host entry
+ *   points, which synchronise the stream before returning.
+ * - Errors: every call returns an ifcm_status and never throws or aborts.
+ *   IFCM_ERR_INVALID is returned for bad arguments before anything is
+ *   launched.  Conditions found on the device (NaN/Inf or constant input
+ *   volume, a bounded wait that ran out) are recorded in a device status word
+ *   inside the workspace; the *_host calls and ifcm_device_status() report it.
+ *   ifcm_last_error() holds a thread-local message for the last failure.
+ */
+#ifndef PIFCM_H
+#define PIFCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IFCM_OK = 0,
+  IFCM_ERR_INVALID = 1,      /* bad argument, shape, parameter or input volume */
+  IFCM_ERR_NOMEM = 2,        /* workspace smaller than *_workspace_bytes()     */
+  IFCM_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed              */
+  IFCM_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out             */
+  IFCM_ERR_BOUNDS = 5,       /* a checked index fell outside its buffer        */
+  IFCM_ERR_UNSUPPORTED = 6   /* valid per the paper but not built (e.g. V > 1) */
+} ifcm_status;
+
+/* Volume geometry.  nz = 1 selects the 2D 8-neighbourhood (Eq 9, L = 3). */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t pitch_x;           /* elements per row, >= nx, multiple of 4 */
+} ifcm_shape;
+
+/* Method parameters (Algorithm 1 / Algorithm 2 inputs). */
+typedef struct {
+  int32_t c;                 /* clusters, 2..8                                   */
+  double m;                  /* fuzzifier m > 1 (Eqs 1-3); m = 2 has a fast path  */
+  int32_t V;                 /* shells of Eq 10; only V = 1 (W_1 = 1) is built    */
+  double h;                  /* decay of Eq 10 (unused for V = 1)                 */
+  int32_t max_iter;          /* IFCM iterations per run, >= 1                     */
+  double eps_u;              /* stop when max_ij |u' - u| < eps_u                 */
+  double dist_floor;         /* lower bound of d^2 (reading R2), e.g. 1e-12       */
+} ifcm_params;
+
+/* Swarm state (Algorithm 1 steps 3-8).  All arrays are device memory owned by
+ * the caller: x, v, pbest_x hold P*2 doubles (lambda, xi per particle),
+ * pbest_f holds P doubles, gen one int32 (the generation counter that keys
+ * the Philox draws). */
+typedef struct {
+  int32_t P;                 /* particles, 1..1024                              */
+  int32_t radius;            /* ring radius of the topological neighbours, >= 0 */
+  double vmax;               /* velocity clamp, > 0                              */
+  uint64_t seed;             /* Philox4x32-10 key                               */
+  double* x;
+  double* v;
+  double* pbest_x;
+  double* pbest_f;
+  int32_t* gen;
+} pso_state;
+
+/* Whole-run options of pifcm3d (Algorithm 1). */
+typedef struct {
+  int32_t P;                 /* particles                                         */
+  int32_t generations;       /* swarm generations (fixed count, reading R9)       */
+  int32_t radius;            /* ring radius                                       */
+  double vmax;               /* velocity clamp                                    */
+  uint64_t seed;             /* Philox key                                        */
+  int32_t init_max_iter;     /* iterations of the FCM start (Algorithm 1 step 2)  */
+  int32_t slice_z;           /* -1: whole volume; else segment slice z as 2D (Algorithm 1 step 1) */
+} pifcm_options;
+
+/* Result block written by pifcm3d (device or host copy). */
+typedef struct {
+  double centres[8];         /* C of the final IFCM run (first c used)            */
+  double lambda, xi;         /* best particle's position                          */
+  double J;                  /* objective of the final run's last iteration       */
+  double best_fitness;       /* lowest personal-best fitness of the swarm         */
+  int64_t updates;           /* voxel x particle x iteration updates executed     */
+  int32_t iters_final;       /* iterations of the final run                       */
+  int32_t iters_init;        /* iterations of the FCM start                       */
+  int32_t status;            /* device status word (an ifcm_status)              */
+  int32_t best_particle;
+} pifcm_result;
+
+const char* ifcm_status_string(ifcm_status s);
+const char* ifcm_last_error(void);
+
+/* Device status word recorded in `ws` by earlier calls (synchronises `stream`). */
+ifcm_status ifcm_device_status(const void* ws, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 2 step 1: x <- (x - min) / (max - min) over the whole volume.
+ * vol: device, read; x_out: device, written (may equal vol).  A NaN/Inf or a
+ * constant volume sets IFCM_ERR_INVALID in the device status word and leaves
+ * x_out unspecified.
+ */
+size_t ifcm_normalize_workspace_bytes(ifcm_shape shape);
+ifcm_status ifcm_normalize(const float* vol, float* x_out, ifcm_shape shape,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * One IFCM run (Eqs 1-10; Algorithm 1 steps 2 and 11).
+ * Iteration t maps (U^t, C^t) to U^{t+1} (Eq 2 with the modified distance of
+ * Eq 4, whose H and F come from U^t by Eqs 5-9), J^t (Eq 1 with that
+ * distance) and C^{t+1} (Eq 3); the run stops when max|U^{t+1} - U^t| <
+ * eps_u or after max_iter iterations.
+ * x:       device, normalised volume [nz][ny][pitch_x].
+ * lam_xi:  device, 2 doubles (lambda, xi), read when the run starts.
+ * u_init:  device [c][nz][ny][pitch_x], or NULL for u_ij = 1/c.
+ * c_init:  device, c doubles, or NULL for c_j = (j + 1/2)/c.
+ * u_out:   device [c][nz][ny][pitch_x] (may be NULL): final memberships.
+ * c_out:   device, c doubles (may be NULL): final centres.
+ * J_out:   device, 1 double (may be NULL): J of the last iteration.
+ * iters_out: device, 1 int32 (may be NULL): iterations executed.
+ * With lambda = xi = 0 this is plain FCM, the start of Algorithm 1 step 2.
+ */
+size_t ifcm_fit_workspace_bytes(ifcm_shape shape, const ifcm_params* p);
+ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
+                     const double* lam_xi, const float* u_init, const double* c_init,
+                     float* u_out, double* c_out, double* J_out, int32_t* iters_out,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* The same run in the shape of the paper's Algorithm 2 (one particle, one
+ * thread per voxel reading its neighbours from global memory, the host
+ * checking convergence after every iteration).  Kept as the plain form that
+ * the batched path is measured against.  Synchronises `stream` each
+ * iteration; lambda and xi are host values; outputs are as for ifcm_fit. */
+ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* p,
+                           double lambda, double xi, const float* u_init,
+                           const double* c_init, float* u_out, double* c_out,
+                           double* J_out, int32_t* iters_out,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 step 4 for a whole swarm: fitness_p = J of an IFCM run from the
+ * shared start (u0, c0) at (lambda_p, xi_p) = lam_xi[2p], lam_xi[2p+1]
+ * (reading R5), all P runs in one batch of launches.
+ * lam_xi: device, P*2 doubles.  u0: device [c][nz][ny][pitch_x].  c0: device,
+ * c doubles.  fitness: device, P doubles.  iters: device, P int32 (may be
+ * NULL).  c_out: device, P*c doubles (may be NULL).
+ */
+size_t pso_fitness_batch_workspace_bytes(ifcm_shape shape, const ifcm_params* p, int32_t P);
+ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_params* p,
+                              const double* lam_xi, int32_t P,
+                              const float* u0, const double* c0,
+                              double* fitness, int32_t* iters, double* c_out,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 step 3: x ~ U[0,1)^2, v ~ U[-vmax, vmax)^2, pbest_x = x,
+ * pbest_f = +inf, gen = 0.  Draws are Philox4x32-10 keyed by seed with
+ * counter (generation, particle, dimension, stream).
+ */
+ifcm_status pso_init(const pso_state* s, void* stream);
+
+/* Algorithm 1 steps 5-8 given fitness (device, P doubles) of the current
+ * positions: strict personal-best update, best of the ring neighbours (ties to
+ * the lowest index), v <- v + p1 (pbest - x) + p2 (lbest - x) clamped to
+ * +-vmax, x <- clip(x + v, 0, 1), gen += 1.  Every operation is one rounded
+ * FP64 operation (no fused multiply-add), so two runs fed the same fitness
+ * values produce bit-identical swarms. */
+ifcm_status pso_step(const pso_state* s, const double* fitness, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 end to end on the device: normalise vol (device, unchanged),
+ * optional slice, FCM start, `generations` x (fitness batch + swarm step),
+ * final IFCM run at the best personal best.  u_out: device
+ * [c][nz'][ny][pitch_x] (nz' = 1 with a slice; may be NULL).  result: device
+ * pifcm_result.
+ */
+size_t pifcm3d_workspace_bytes(ifcm_shape shape, const ifcm_params* p, const pifcm_options* o);
+ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
+                    const pifcm_options* o, float* u_out, pifcm_result* result,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* The same with HOST input and outputs: copies vol_host in, runs pifcm3d and
+ * copies the memberships and the result block back, then synchronises the
+ * stream.  The workspace also holds the device copies of the volume, the
+ * memberships and the result (size from pifcm3d_host_workspace_bytes()).
+ * vol_host / u_out_host should be page-locked for full copy speed.
+ * u_out_host may be NULL.  Returns the device status word's error, if any. */
+size_t pifcm3d_host_workspace_bytes(ifcm_shape shape, const ifcm_params* p,
+                                    const pifcm_options* o);
+ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_params* p,
+                         const pifcm_options* o, float* u_out_host,
+                         pifcm_result* result_host,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Profiling counters (host side, per process): when enabled, the library
+ * records CUDA events around every launch of the stencil-iteration kernel
+ * and the updates it was launched for; ifcm_profile_read() synchronises the
+ * recorded events and returns the summed kernel milliseconds, launches and
+ * the voxel x particle updates processed (from the device counters).
+ */
+void ifcm_profile_enable(int32_t on);
+ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIFCM_H */

@@ -1,0 +1,771 @@
+// C ABI of the 3DPIFCM library (declared in include/pifcm.h): argument checks,
+// workspace layout, TMA tensor maps and the launch sequences of the path.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "launch.h"
+
+using namespace pifcm;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+ifcm_status fail(ifcm_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU_TRY(expr)                                                                  \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(IFCM_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                \
+  } while (0)
+
+#define ST_TRY(expr)                 \
+  do {                               \
+    ifcm_status s_ = (expr);         \
+    if (s_ != IFCM_OK) return s_;    \
+  } while (0)
+
+// ------------------------------------------------------------ validation
+ifcm_status check_shape(const ifcm_shape& s) {
+  if (s.nx < 1 || s.ny < 1 || s.nz < 1)
+    return fail(IFCM_ERR_INVALID, "shape %dx%dx%d: every extent must be >= 1", s.nx, s.ny, s.nz);
+  if (s.pitch_x < s.nx || s.pitch_x % 4 != 0)
+    return fail(IFCM_ERR_INVALID, "pitch_x %d must be >= nx (%d) and a multiple of 4",
+                s.pitch_x, s.nx);
+  const double elems = static_cast<double>(s.pitch_x) * s.ny * s.nz;
+  if (elems > 4.0e9)
+    return fail(IFCM_ERR_INVALID, "volume of %.0f elements exceeds the 4e9 limit", elems);
+  return IFCM_OK;
+}
+
+ifcm_status check_params(const ifcm_params* p) {
+  if (!p) return fail(IFCM_ERR_INVALID, "params is NULL");
+  if (p->c < 2 || p->c > kMaxC) return fail(IFCM_ERR_INVALID, "c = %d outside 2..%d", p->c, kMaxC);
+  if (!(p->m > 1.0) || !std::isfinite(p->m))
+    return fail(IFCM_ERR_INVALID, "fuzzifier m = %g must be finite and > 1", p->m);
+  if (p->V != 1)
+    return fail(IFCM_ERR_UNSUPPORTED, "V = %d shells: only V = 1 is built", p->V);
+  if (p->max_iter < 1) return fail(IFCM_ERR_INVALID, "max_iter = %d must be >= 1", p->max_iter);
+  if (!(p->eps_u >= 0.0)) return fail(IFCM_ERR_INVALID, "eps_u = %g must be >= 0", p->eps_u);
+  if (!(p->dist_floor > 0.0) || !(p->dist_floor < 1.0))
+    return fail(IFCM_ERR_INVALID, "dist_floor = %g must lie in (0, 1)", p->dist_floor);
+  return IFCM_OK;
+}
+
+ifcm_status check_aligned(const void* ptr, const char* what) {
+  if (!ptr) return fail(IFCM_ERR_INVALID, "%s is NULL", what);
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0)
+    return fail(IFCM_ERR_INVALID, "%s must be 16-byte aligned", what);
+  return IFCM_OK;
+}
+
+// ------------------------------------------------------------- workspace
+struct Carver {
+  uintptr_t base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(reinterpret_cast<uintptr_t>(b)) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+size_t plane_elems(const ifcm_shape& s) {
+  return static_cast<size_t>(s.nz) * s.ny * s.pitch_x;
+}
+
+struct Tiling {
+  int tiles_x, tiles_y, zchunks, tz, n_tiles;
+};
+
+Tiling tiling(const ifcm_shape& s) {
+  Tiling t;
+  t.tiles_x = (s.nx + kTX - 1) / kTX;
+  t.tiles_y = (s.ny + kTY - 1) / kTY;
+  t.tz = s.nz < 32 ? s.nz : 32;
+  t.zchunks = (s.nz + t.tz - 1) / t.tz;
+  t.n_tiles = t.tiles_x * t.tiles_y * t.zchunks;
+  return t;
+}
+
+constexpr int kPlainVpt = 32;
+
+// Buffers of a batch of IFCM runs (P particles).
+struct RunBufs {
+  float* ua;
+  float* ub;
+  double* partials;
+  float* dmax;
+  RunState st;
+  int n_rec;
+};
+
+RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P) {
+  RunBufs r;
+  const size_t pl = plane_elems(s);
+  r.ua = cv.take<float>(static_cast<size_t>(P) * c * pl);
+  r.ub = cv.take<float>(static_cast<size_t>(P) * c * pl);
+  const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  const int nrec_stencil = tiling(s).n_tiles;
+  const int nrec_plain = plain_blocks(nvox, kPlainVpt);
+  r.n_rec = nrec_stencil > nrec_plain ? nrec_stencil : nrec_plain;
+  r.partials = cv.take<double>(static_cast<size_t>(P) * r.n_rec * (2 * c + 1));
+  r.dmax = cv.take<float>(static_cast<size_t>(P) * r.n_rec);
+  r.st.centres = cv.take<double>(static_cast<size_t>(P) * c);
+  r.st.J = cv.take<double>(P);
+  r.st.active = cv.take<int32_t>(P);
+  r.st.iters = cv.take<int32_t>(P);
+  r.st.updates = cv.take<unsigned long long>(1);
+  return r;
+}
+
+DevStatus* carve_status(Carver& cv) { return cv.take<DevStatus>(1); }
+
+struct NormBufs {
+  float* pmin;
+  float* pmax;
+  int32_t* pbad;
+  int nparts;
+};
+
+NormBufs carve_norm(Carver& cv, const ifcm_shape& s) {
+  NormBufs n;
+  const long long rows = static_cast<long long>(s.ny) * s.nz;
+  n.nparts = static_cast<int>(rows < 1024 ? rows : 1024);
+  n.pmin = cv.take<float>(n.nparts);
+  n.pmax = cv.take<float>(n.nparts);
+  n.pbad = cv.take<int32_t>(n.nparts);
+  return n;
+}
+
+// ------------------------------------------------------------ tensor maps
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+ifcm_status get_encode() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return fail(IFCM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  return IFCM_OK;
+}
+
+// Box of one stencil plane: TX + 8 columns (4-voxel aligned margins) by TY + 2 rows.
+constexpr cuuint32_t kBoxX = kTX + 8, kBoxY = kTY + 2;
+
+ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int planes,
+                     int box_planes) {
+  ST_TRY(get_encode());
+  const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * 4;
+  if (planes <= 0) {   // 3D volume map
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
+                          static_cast<cuuint64_t>(s.nz)};
+    cuuint64_t strides[2] = {row, row * s.ny};
+    cuuint32_t box[3] = {kBoxX, kBoxY, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (volume) failed: %d", (int)r);
+    return IFCM_OK;
+  }
+  cuuint64_t dims[4] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
+                        static_cast<cuuint64_t>(s.nz), static_cast<cuuint64_t>(planes)};
+  cuuint64_t strides[3] = {row, row * s.ny, row * s.ny * s.nz};
+  cuuint32_t box[4] = {kBoxX, kBoxY, 1, static_cast<cuuint32_t>(box_planes)};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (memberships) failed: %d", (int)r);
+  return IFCM_OK;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// ------------------------------------------------------------ profiling
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used, spare;
+} g_prof;
+
+cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on) return nullptr;
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (!g_prof.spare.empty()) {
+    ev = g_prof.spare.back();
+    g_prof.spare.pop_back();
+  } else {
+    cudaEventCreate(&ev.first);
+    cudaEventCreate(&ev.second);
+  }
+  g_prof.used.push_back(ev);
+  cudaEventRecord(ev.first, s);
+  *end_out = ev.second;
+  return ev.first;
+}
+
+// ------------------------------------------------------------ run loops
+ifcm_status fill_method(StencilArgs& a, const ifcm_params* p) {
+  a.dist_floor = static_cast<float>(p->dist_floor);
+  a.m = static_cast<float>(p->m);
+  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
+  a.m_is_2 = p->m == 2.0;
+  return IFCM_OK;
+}
+
+// IFCM runs of P particles with the stencil kernel from the shared start
+// (u0 [c][plane], c0 [c] or NULL).
+ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* p,
+                        const double* lam_xi, int P, const float* u0, const double* c0,
+                        RunBufs& rb, double* fitness, int32_t* iters, double* c_out,
+                        DevStatus* status, cudaStream_t st) {
+  const int c = p->c;
+  const Tiling t = tiling(s);
+  const size_t pl = plane_elems(s);
+  CUtensorMap tm_x, tm_u0, tm_ua, tm_ub;
+  ST_TRY(make_map(&tm_x, x, s, 0, 0));
+  ST_TRY(make_map(&tm_u0, u0, s, c, c));
+  ST_TRY(make_map(&tm_ua, rb.ua, s, P * c, c));
+  ST_TRY(make_map(&tm_ub, rb.ub, s, P * c, c));
+  CU_TRY(launch_run_init(c, P, c0, rb.st, nullptr, st));
+
+  StencilArgs a{};
+  a.nx = s.nx;
+  a.ny = s.ny;
+  a.nz = s.nz;
+  a.pitch = s.pitch_x;
+  a.tiles_x = t.tiles_x;
+  a.tiles_y = t.tiles_y;
+  a.zchunks = t.zchunks;
+  a.tz = t.tz;
+  a.n_tiles = t.n_tiles;
+  a.P = P;
+  a.lam_xi = lam_xi;
+  a.centres = rb.st.centres;
+  a.active = rb.st.active;
+  a.partials = rb.partials;
+  a.dmax = rb.dmax;
+  a.status = status;
+  fill_method(a, p);
+
+  ReduceArgs r{};
+  r.P = P;
+  r.n_rec = t.n_tiles;
+  r.partials = rb.partials;
+  r.dmax = rb.dmax;
+  r.st = rb.st;
+  r.fitness = fitness;
+  r.iters_out = iters;
+  r.c_out = c_out;
+  r.max_iter = p->max_iter;
+  r.eps = p->eps_u;
+  r.nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  r.status = status;
+
+  const long long items = static_cast<long long>(P) * t.n_tiles;
+  long long grid = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c);
+  if (grid > items) grid = items;
+
+  for (int it = 0; it < p->max_iter; ++it) {
+    const bool first = it == 0;
+    a.u_dst = (it % 2 == 0) ? rb.ua : rb.ub;
+    a.u_src = first ? u0 : ((it % 2 == 1) ? rb.ua : rb.ub);
+    a.src_pstride = first ? 0 : static_cast<long long>(c) * pl;
+    a.src_cstride = first ? 0 : c;
+    const CUtensorMap& tm_u = first ? tm_u0 : ((it % 2 == 1) ? tm_ua : tm_ub);
+    cudaEvent_t ev_end = nullptr;
+    cudaEvent_t ev_beg = prof_begin(st, &ev_end);
+    CU_TRY(launch_stencil(c, tm_x, tm_u, a, static_cast<int>(grid), st));
+    if (ev_beg) cudaEventRecord(ev_end, st);
+    CU_TRY(launch_reduce(c, r, st));
+  }
+  return IFCM_OK;
+}
+
+// One run with the plain kernel (P = 1).  host_check: read max|du| after
+// every iteration and stop on the host (the paper's Algorithm 2 loop).
+ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
+                      const double* lam_xi_dev, float lam, float xi, bool stencil,
+                      const float* u_init, const double* c_init, int max_iter, RunBufs& rb,
+                      int32_t* iters_out, double* c_out, double* J_out, DevStatus* status,
+                      bool host_check, cudaStream_t st) {
+  const int c = p->c;
+  const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  const int blocks = plain_blocks(nvox, kPlainVpt);
+  CU_TRY(launch_run_init(c, 1, c_init, rb.st, nullptr, st));
+  PlainArgs a{};
+  a.nx = s.nx;
+  a.ny = s.ny;
+  a.nz = s.nz;
+  a.pitch = s.pitch_x;
+  a.x = x;
+  a.lam_xi = lam_xi_dev;
+  a.lam = lam;
+  a.xi = xi;
+  a.centres = rb.st.centres;
+  a.active = rb.st.active;
+  a.partials = rb.partials;
+  a.dmax = rb.dmax;
+  a.dist_floor = static_cast<float>(p->dist_floor);
+  a.m = static_cast<float>(p->m);
+  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
+  a.m_is_2 = p->m == 2.0;
+  a.vpt = kPlainVpt;
+  a.stencil = stencil ? 1 : 0;
+  a.status = status;
+  ReduceArgs r{};
+  r.P = 1;
+  r.n_rec = blocks;
+  r.partials = rb.partials;
+  r.dmax = rb.dmax;
+  r.st = rb.st;
+  r.fitness = J_out;
+  r.iters_out = iters_out;
+  r.c_out = c_out;
+  r.max_iter = max_iter;
+  r.eps = p->eps_u;
+  r.nvox = nvox;
+  r.status = status;
+  for (int it = 0; it < max_iter; ++it) {
+    a.u_dst = (it % 2 == 0) ? rb.ua : rb.ub;
+    a.u_src = it == 0 ? u_init : ((it % 2 == 1) ? rb.ua : rb.ub);
+    CU_TRY(launch_plain(c, a, blocks, st));
+    CU_TRY(launch_reduce(c, r, st));
+    if (host_check) {
+      int32_t act = 0;
+      CU_TRY(cudaMemcpyAsync(&act, rb.st.active, sizeof(act), cudaMemcpyDeviceToHost, st));
+      CU_TRY(cudaStreamSynchronize(st));
+      if (!act) break;
+    }
+  }
+  return IFCM_OK;
+}
+
+// ------------------------------------------------------------ pifcm3d layout
+struct PifcmBufs {
+  DevStatus* status;
+  float* x;
+  float* u0;
+  double* c0;
+  double* sw_x;
+  double* sw_v;
+  double* sw_pbx;
+  double* sw_pbf;
+  int32_t* sw_gen;
+  double* fitness;
+  int32_t* iters;
+  double* lam_best;
+  int32_t* best;
+  int32_t* iters_init;
+  int32_t* iters_final;
+  double* J_final;
+  double* c_final;
+  double* J_init;
+  unsigned long long* updates;
+  NormBufs norm;
+  RunBufs run;
+};
+
+ifcm_shape run_shape(const ifcm_shape& s, const pifcm_options* o) {
+  ifcm_shape r = s;
+  if (o->slice_z >= 0) r.nz = 1;
+  return r;
+}
+
+PifcmBufs carve_pifcm(Carver& cv, const ifcm_shape& s, const ifcm_params* p,
+                      const pifcm_options* o) {
+  PifcmBufs b;
+  const int c = p->c, P = o->P;
+  const ifcm_shape rs = run_shape(s, o);
+  b.status = carve_status(cv);
+  b.x = cv.take<float>(plane_elems(s));
+  b.u0 = cv.take<float>(static_cast<size_t>(c) * plane_elems(rs));
+  b.c0 = cv.take<double>(c);
+  b.sw_x = cv.take<double>(2 * P);
+  b.sw_v = cv.take<double>(2 * P);
+  b.sw_pbx = cv.take<double>(2 * P);
+  b.sw_pbf = cv.take<double>(P);
+  b.sw_gen = cv.take<int32_t>(1);
+  b.fitness = cv.take<double>(P);
+  b.iters = cv.take<int32_t>(P);
+  b.lam_best = cv.take<double>(2);
+  b.best = cv.take<int32_t>(1);
+  b.iters_init = cv.take<int32_t>(1);
+  b.iters_final = cv.take<int32_t>(1);
+  b.J_final = cv.take<double>(1);
+  b.c_final = cv.take<double>(c);
+  b.J_init = cv.take<double>(1);
+  b.updates = cv.take<unsigned long long>(1);
+  b.norm = carve_norm(cv, s);
+  b.run = carve_run(cv, rs, c, P);
+  return b;
+}
+
+ifcm_status check_options(const pifcm_options* o, const ifcm_shape& s) {
+  if (!o) return fail(IFCM_ERR_INVALID, "options is NULL");
+  if (o->P < 1 || o->P > kMaxP) return fail(IFCM_ERR_INVALID, "P = %d outside 1..%d", o->P, kMaxP);
+  if (o->generations < 1) return fail(IFCM_ERR_INVALID, "generations must be >= 1");
+  if (o->radius < 0) return fail(IFCM_ERR_INVALID, "radius must be >= 0");
+  if (!(o->vmax > 0.0)) return fail(IFCM_ERR_INVALID, "vmax must be > 0");
+  if (o->init_max_iter < 1) return fail(IFCM_ERR_INVALID, "init_max_iter must be >= 1");
+  if (o->slice_z >= s.nz) return fail(IFCM_ERR_INVALID, "slice_z %d >= nz %d", o->slice_z, s.nz);
+  return IFCM_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* ifcm_status_string(ifcm_status s) {
+  switch (s) {
+    case IFCM_OK: return "ok";
+    case IFCM_ERR_INVALID: return "invalid argument or input";
+    case IFCM_ERR_NOMEM: return "workspace too small";
+    case IFCM_ERR_CUDA: return "CUDA error";
+    case IFCM_ERR_TIMEOUT: return "device wait timed out";
+    case IFCM_ERR_BOUNDS: return "index out of bounds";
+    case IFCM_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* ifcm_last_error(void) { return g_msg; }
+
+ifcm_status ifcm_device_status(const void* ws, void* stream) {
+  if (!ws) return fail(IFCM_ERR_INVALID, "ws is NULL");
+  DevStatus h{};
+  CU_TRY(cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost,
+                         static_cast<cudaStream_t>(stream)));
+  CU_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  if (h.status != 0)
+    return fail(static_cast<ifcm_status>(h.status), "device status %d (site %d)", h.status,
+                h.where);
+  return IFCM_OK;
+}
+
+// ---------------------------------------------------------- normalise
+size_t ifcm_normalize_workspace_bytes(ifcm_shape shape) {
+  Carver cv(nullptr);
+  carve_status(cv);
+  carve_norm(cv, shape);
+  return cv.off + 256;
+}
+
+ifcm_status ifcm_normalize(const float* vol, float* x_out, ifcm_shape shape, void* ws,
+                           size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_aligned(vol, "vol"));
+  ST_TRY(check_aligned(x_out, "x_out"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (ws_bytes < ifcm_normalize_workspace_bytes(shape))
+    return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes,
+                ifcm_normalize_workspace_bytes(shape));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  DevStatus* status = carve_status(cv);
+  NormBufs n = carve_norm(cv, shape);
+  CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
+  CU_TRY(launch_minmax(vol, shape.nx, shape.ny, shape.nz, shape.pitch_x, n.pmin, n.pmax, n.pbad,
+                       n.nparts, st));
+  CU_TRY(launch_scale(vol, x_out, shape.nx, shape.ny, shape.nz, shape.pitch_x, n.pmin, n.pmax,
+                      n.pbad, n.nparts, status, st));
+  return IFCM_OK;
+}
+
+// ----------------------------------------------------------- ifcm_fit
+size_t ifcm_fit_workspace_bytes(ifcm_shape shape, const ifcm_params* p) {
+  if (!p || p->c < 2 || p->c > kMaxC) return 0;
+  Carver cv(nullptr);
+  carve_status(cv);
+  cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));   // uniform start
+  carve_run(cv, shape, p->c, 1);
+  return cv.off + 256;
+}
+
+ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
+                     const double* lam_xi, const float* u_init, const double* c_init,
+                     float* u_out, double* c_out, double* J_out, int32_t* iters_out, void* ws,
+                     size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  ST_TRY(check_aligned(x, "x"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (!lam_xi) return fail(IFCM_ERR_INVALID, "lam_xi is NULL");
+  if (u_init) ST_TRY(check_aligned(u_init, "u_init"));
+  if (u_out) ST_TRY(check_aligned(u_out, "u_out"));
+  const size_t need = ifcm_fit_workspace_bytes(shape, p);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  DevStatus* status = carve_status(cv);
+  float* uni = cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
+  RunBufs rb = carve_run(cv, shape, p->c, 1);
+  CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
+  const float* start = u_init;
+  if (!start) {
+    CU_TRY(launch_fill(uni, 1.0f / p->c, static_cast<long long>(p->c) * plane_elems(shape), st));
+    start = uni;
+  }
+  ST_TRY(run_stencil(x, shape, p, lam_xi, 1, start, c_init, rb, J_out, iters_out, c_out, status,
+                     st));
+  if (u_out)
+    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out,
+                              static_cast<long long>(p->c) * plane_elems(shape), st));
+  return IFCM_OK;
+}
+
+ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* p, double lambda,
+                           double xi, const float* u_init, const double* c_init, float* u_out,
+                           double* c_out, double* J_out, int32_t* iters_out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  ST_TRY(check_aligned(x, "x"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (u_out) ST_TRY(check_aligned(u_out, "u_out"));
+  const size_t need = ifcm_fit_workspace_bytes(shape, p);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  DevStatus* status = carve_status(cv);
+  cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
+  RunBufs rb = carve_run(cv, shape, p->c, 1);
+  CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
+  ST_TRY(run_plain(x, shape, p, nullptr, static_cast<float>(lambda), static_cast<float>(xi),
+                   true, u_init, c_init, p->max_iter, rb, iters_out, c_out, J_out, status,
+                   true, st));
+  if (u_out)
+    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out,
+                              static_cast<long long>(p->c) * plane_elems(shape), st));
+  return IFCM_OK;
+}
+
+// -------------------------------------------------- pso_fitness_batch
+size_t pso_fitness_batch_workspace_bytes(ifcm_shape shape, const ifcm_params* p, int32_t P) {
+  if (!p || p->c < 2 || p->c > kMaxC || P < 1) return 0;
+  Carver cv(nullptr);
+  carve_status(cv);
+  carve_run(cv, shape, p->c, P);
+  return cv.off + 256;
+}
+
+ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_params* p,
+                              const double* lam_xi, int32_t P, const float* u0,
+                              const double* c0, double* fitness, int32_t* iters,
+                              double* c_out, void* ws, size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  if (P < 1 || P > kMaxP) return fail(IFCM_ERR_INVALID, "P = %d outside 1..%d", P, kMaxP);
+  ST_TRY(check_aligned(x, "x"));
+  ST_TRY(check_aligned(u0, "u0"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (!lam_xi || !c0 || !fitness)
+    return fail(IFCM_ERR_INVALID, "lam_xi, c0 and fitness must not be NULL");
+  const size_t need = pso_fitness_batch_workspace_bytes(shape, p, P);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  DevStatus* status = carve_status(cv);
+  RunBufs rb = carve_run(cv, shape, p->c, P);
+  CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
+  return run_stencil(x, shape, p, lam_xi, P, u0, c0, rb, fitness, iters, c_out, status, st);
+}
+
+// ------------------------------------------------------------- swarm
+static ifcm_status check_swarm(const pso_state* s) {
+  if (!s) return fail(IFCM_ERR_INVALID, "swarm is NULL");
+  if (s->P < 1 || s->P > kMaxP) return fail(IFCM_ERR_INVALID, "P = %d outside 1..%d", s->P, kMaxP);
+  if (s->radius < 0) return fail(IFCM_ERR_INVALID, "radius must be >= 0");
+  if (!(s->vmax > 0.0)) return fail(IFCM_ERR_INVALID, "vmax must be > 0");
+  if (!s->x || !s->v || !s->pbest_x || !s->pbest_f || !s->gen)
+    return fail(IFCM_ERR_INVALID, "swarm arrays must not be NULL");
+  return IFCM_OK;
+}
+
+ifcm_status pso_init(const pso_state* s, void* stream) {
+  ST_TRY(check_swarm(s));
+  CU_TRY(launch_pso_init(*s, static_cast<cudaStream_t>(stream)));
+  return IFCM_OK;
+}
+
+ifcm_status pso_step(const pso_state* s, const double* fitness, void* stream) {
+  ST_TRY(check_swarm(s));
+  if (!fitness) return fail(IFCM_ERR_INVALID, "fitness is NULL");
+  CU_TRY(launch_pso_step(*s, fitness, static_cast<cudaStream_t>(stream)));
+  return IFCM_OK;
+}
+
+// ------------------------------------------------------------ pifcm3d
+size_t pifcm3d_workspace_bytes(ifcm_shape shape, const ifcm_params* p, const pifcm_options* o) {
+  if (!p || !o || p->c < 2 || p->c > kMaxC || o->P < 1) return 0;
+  Carver cv(nullptr);
+  carve_pifcm(cv, shape, p, o);
+  return cv.off + 256;
+}
+
+ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
+                    const pifcm_options* o, float* u_out, pifcm_result* result, void* ws,
+                    size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  ST_TRY(check_options(o, shape));
+  ST_TRY(check_aligned(vol, "vol"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (u_out) ST_TRY(check_aligned(u_out, "u_out"));
+  if (!result) return fail(IFCM_ERR_INVALID, "result is NULL");
+  const size_t need = pifcm3d_workspace_bytes(shape, p, o);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int c = p->c, P = o->P;
+  Carver cv(ws);
+  PifcmBufs b = carve_pifcm(cv, shape, p, o);
+  const ifcm_shape rs = run_shape(shape, o);
+  const size_t rpl = plane_elems(rs);
+
+  CU_TRY(cudaMemsetAsync(b.status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(b.updates, 0, sizeof(unsigned long long), st));
+  // Algorithm 2 step 1: normalise over the whole volume, then (Alg 1 step 1) slice.
+  CU_TRY(launch_minmax(vol, shape.nx, shape.ny, shape.nz, shape.pitch_x, b.norm.pmin,
+                       b.norm.pmax, b.norm.pbad, b.norm.nparts, st));
+  CU_TRY(launch_scale(vol, b.x, shape.nx, shape.ny, shape.nz, shape.pitch_x, b.norm.pmin,
+                      b.norm.pmax, b.norm.pbad, b.norm.nparts, b.status, st));
+  const float* xr =
+      o->slice_z >= 0 ? b.x + static_cast<size_t>(o->slice_z) * shape.ny * shape.pitch_x : b.x;
+
+  RunBufs rb = b.run;
+  rb.st.updates = b.updates;
+  // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c.
+  ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter, rb,
+                   b.iters_init, b.c0, b.J_init, b.status, false, st));
+  CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, b.u0, static_cast<long long>(c) * rpl, st));
+
+  // Algorithm 1 steps 3-9.
+  pso_state sw{};
+  sw.P = P;
+  sw.radius = o->radius;
+  sw.vmax = o->vmax;
+  sw.seed = o->seed;
+  sw.x = b.sw_x;
+  sw.v = b.sw_v;
+  sw.pbest_x = b.sw_pbx;
+  sw.pbest_f = b.sw_pbf;
+  sw.gen = b.sw_gen;
+  CU_TRY(launch_pso_init(sw, st));
+  for (int g = 0; g < o->generations; ++g) {
+    ST_TRY(run_stencil(xr, rs, p, sw.x, P, b.u0, b.c0, rb, b.fitness, b.iters, nullptr, b.status,
+                       st));
+    CU_TRY(launch_pso_step(sw, b.fitness, st));
+  }
+  // Algorithm 1 step 11: final IFCM at the best personal best.
+  CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));
+  ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
+                     b.c_final, b.status, st));
+  if (u_out)
+    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out, static_cast<long long>(c) * rpl,
+                              st));
+  CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
+                       b.iters_init, b.updates, b.best, b.status, result, st));
+  return IFCM_OK;
+}
+
+size_t pifcm3d_host_workspace_bytes(ifcm_shape shape, const ifcm_params* p,
+                                    const pifcm_options* o) {
+  if (!p || !o || p->c < 2 || p->c > kMaxC || o->P < 1) return 0;
+  Carver cv(nullptr);
+  cv.take<float>(plane_elems(shape));
+  cv.take<float>(static_cast<size_t>(p->c) * plane_elems(run_shape(shape, o)));
+  cv.take<pifcm_result>(1);
+  cv.take<unsigned char>(pifcm3d_workspace_bytes(shape, p, o));
+  return cv.off + 256;
+}
+
+ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_params* p,
+                         const pifcm_options* o, float* u_out_host, pifcm_result* result_host,
+                         void* ws, size_t ws_bytes, void* stream) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  ST_TRY(check_options(o, shape));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (!vol_host || !result_host) return fail(IFCM_ERR_INVALID, "vol_host / result_host is NULL");
+  const size_t need = pifcm3d_host_workspace_bytes(shape, p, o);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  const size_t upl = static_cast<size_t>(p->c) * plane_elems(run_shape(shape, o));
+  float* vol = cv.take<float>(plane_elems(shape));
+  float* u = cv.take<float>(upl);
+  pifcm_result* res = cv.take<pifcm_result>(1);
+  const size_t inner = pifcm3d_workspace_bytes(shape, p, o);
+  void* iws = cv.take<unsigned char>(inner);
+  CU_TRY(cudaMemcpyAsync(vol, vol_host, plane_elems(shape) * sizeof(float),
+                         cudaMemcpyHostToDevice, st));
+  ST_TRY(pifcm3d(vol, shape, p, o, u_out_host ? u : nullptr, res, iws, inner, stream));
+  if (u_out_host)
+    CU_TRY(cudaMemcpyAsync(u_out_host, u, upl * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CU_TRY(cudaMemcpyAsync(result_host, res, sizeof(pifcm_result), cudaMemcpyDeviceToHost, st));
+  CU_TRY(cudaStreamSynchronize(st));
+  if (result_host->status != 0)
+    return fail(static_cast<ifcm_status>(result_host->status), "device status %d",
+                result_host->status);
+  return IFCM_OK;
+}
+
+// ------------------------------------------------------------ profiling
+void ifcm_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = on != 0;
+}
+
+ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  double total = 0.0;
+  for (auto& ev : g_prof.used) {
+    CU_TRY(cudaEventSynchronize(ev.second));
+    float ms = 0.0f;
+    CU_TRY(cudaEventElapsedTime(&ms, ev.first, ev.second));
+    total += ms;
+    g_prof.spare.push_back(ev);
+  }
+  if (kernel_ms) *kernel_ms = total;
+  if (launches) *launches = static_cast<int64_t>(g_prof.used.size());
+  g_prof.used.clear();
+  return IFCM_OK;
+}
+
+}  // extern "C"

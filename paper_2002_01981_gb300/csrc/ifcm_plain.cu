@@ -1,0 +1,238 @@
+// The plain IFCM iteration (one thread per voxel, neighbours read straight
+// from global memory: the shape of the paper's Algorithm 2 steps 6-8), the
+// per-particle reduction that finalises every iteration (Eq 3 centres, Eq 1
+// objective, stop rule), and the run-state initialisation.
+#include "ifcm_math.cuh"
+#include "launch.h"
+
+namespace pifcm {
+
+namespace {
+
+constexpr int PT = 256;   // threads per block of the plain kernel
+
+template <int C>
+__global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
+  __shared__ float s_red[PT / 32][2 * C + 2];
+  if (!a.active[0]) return;
+  const long long nvox = static_cast<long long>(a.nx) * a.ny * a.nz;
+  const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
+  MethodConsts k;
+  if (a.lam_xi) {
+    k.lam = static_cast<float>(a.lam_xi[0]);
+    k.xi = static_cast<float>(a.lam_xi[1]);
+  } else {
+    k.lam = a.lam;
+    k.xi = a.xi;
+  }
+  k.dist_floor = a.dist_floor;
+  k.m = a.m;
+  k.inv_m1 = a.inv_m1;
+  k.m_is_2 = a.m_is_2;
+  float cc[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) cc[j] = static_cast<float>(a.centres[j]);
+  const bool stencil = a.stencil && (k.lam != 0.0f || k.xi != 0.0f);
+
+  float s0[C], s1[C], Js = 0.0f, dm = 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) s0[j] = s1[j] = 0.0f;
+
+  const long long first = static_cast<long long>(blockIdx.x) * PT * a.vpt;
+  for (int r = 0; r < a.vpt; ++r) {
+    const long long i = first + static_cast<long long>(r) * PT + threadIdx.x;
+    if (i >= nvox) break;
+    const int X = static_cast<int>(i % a.nx);
+    const long long yz = i / a.nx;
+    const int Y = static_cast<int>(yz % a.ny);
+    const int Z = static_cast<int>(yz / a.ny);
+    const size_t off = (static_cast<size_t>(Z) * a.ny + Y) * a.pitch + X;
+    const float xc = a.x[off];
+    float uc[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) uc[j] = a.u_src ? a.u_src[j * plane + off] : 1.0f / C;
+    float H[C], F[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
+    if (stencil) {
+      float G = 0.0f, Q = 0.0f;
+      int cnt = 0;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+            if (kx < 0 || kx >= a.nx || ky < 0 || ky >= a.ny || kz < 0 || kz >= a.nz) continue;
+            const size_t ko = (static_cast<size_t>(kz) * a.ny + ky) * a.pitch + kx;
+            const float g = fabsf(xc - a.x[ko]);                       // Eq 6
+            const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);   // Eq 8
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+              const float uk = a.u_src ? a.u_src[j * plane + ko] : 1.0f / C;
+              H[j] = fmaf(uk, g, H[j]);
+              F[j] = fmaf(uk * uk, q2, F[j]);
+            }
+            G += g;
+            Q += q2;
+            ++cnt;
+          }
+      if (cnt > 0) {
+        const float invQ = __frcp_rn(Q);
+#pragma unroll
+        for (int j = 0; j < C; ++j) F[j] *= invQ;
+        if (G > 0.0f) {
+          const float invG = __frcp_rn(G);
+#pragma unroll
+          for (int j = 0; j < C; ++j) H[j] *= invG;
+        } else if (a.u_src) {
+          flat_neighbourhood_mean<C>(a.u_src, X, Y, Z, a.nx, a.ny, a.nz, a.pitch, H);
+        } else {
+#pragma unroll
+          for (int j = 0; j < C; ++j) H[j] = 1.0f / C;
+        }
+      }
+    }
+    float u[C], um[C], Jv;
+    voxel_update<C>(H, F, xc, cc, k, u, um, Jv);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      a.u_dst[j * plane + off] = u[j];
+      s0[j] += um[j];
+      s1[j] = fmaf(um[j], xc, s1[j]);
+      dm = fmaxf(dm, fabsf(u[j] - uc[j]));
+    }
+    Js += Jv;
+  }
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float v0 = warp_sum(s0[j]);
+    const float v1 = warp_sum(s1[j]);
+    if (lane == 0) {
+      s_red[warp][j] = v0;
+      s_red[warp][C + j] = v1;
+    }
+  }
+  const float vj = warp_sum(Js);
+  const float vm = warp_max(dm);
+  if (lane == 0) {
+    s_red[warp][2 * C] = vj;
+    s_red[warp][2 * C + 1] = vm;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * C + 1) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < PT / 32; ++w) sum += static_cast<double>(s_red[w][threadIdx.x]);
+    a.partials[static_cast<size_t>(blockIdx.x) * (2 * C + 1) + threadIdx.x] = sum;
+  } else if (threadIdx.x == 2 * C + 1) {
+    float mm = 0.0f;
+#pragma unroll
+    for (int w = 0; w < PT / 32; ++w) mm = fmaxf(mm, s_red[w][2 * C + 1]);
+    a.dmax[blockIdx.x] = mm;
+  }
+}
+
+// One block per particle: FP64 sum of the particle's partial records in a
+// fixed order (so the result does not depend on scheduling), then Eq 3
+// centres, the Eq 1 objective, and the stop rule of the run.
+constexpr int RT = 256;
+
+template <int C>
+__global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
+  constexpr int NV = 2 * C + 1;
+  __shared__ double s_sum[NV][RT];
+  __shared__ float s_max[RT];
+  const int p = blockIdx.x;
+  if (!a.st.active[p]) return;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  float mx = 0.0f;
+  const double* rec = a.partials + static_cast<size_t>(p) * a.n_rec * NV;
+  for (int r = threadIdx.x; r < a.n_rec; r += RT) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += rec[static_cast<size_t>(r) * NV + v];
+    mx = fmaxf(mx, a.dmax[static_cast<size_t>(p) * a.n_rec + r]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = acc[v];
+  s_max[threadIdx.x] = mx;
+  __syncthreads();
+  for (int h = RT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] += s_sum[v][threadIdx.x + h];
+      s_max[threadIdx.x] = fmaxf(s_max[threadIdx.x], s_max[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* cen = a.st.centres + static_cast<size_t>(p) * C;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const double S0 = s_sum[j][0], S1 = s_sum[C + j][0];
+      if (S0 > 0.0) cen[j] = S1 / S0;                        // Eq 3
+      if (a.c_out) a.c_out[static_cast<size_t>(p) * C + j] = cen[j];
+    }
+    const double J = s_sum[2 * C][0];                       // Eq 1
+    a.st.J[p] = J;
+    const int it = a.st.iters[p] + 1;
+    a.st.iters[p] = it;
+    if (a.fitness) a.fitness[p] = J;
+    if (a.iters_out) a.iters_out[p] = it;
+    const double delta = static_cast<double>(s_max[0]);
+    if (!(delta >= a.eps) || it >= a.max_iter) a.st.active[p] = 0;
+    atomicAdd(a.st.updates, static_cast<unsigned long long>(a.nvox));
+  }
+}
+
+template <int C>
+__global__ void run_init_kernel(int P, const double* c0, RunState st, double* J_clear) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+#pragma unroll
+  for (int j = 0; j < C; ++j)
+    st.centres[static_cast<size_t>(p) * C + j] = c0 ? c0[j] : (j + 0.5) / C;
+  st.active[p] = 1;
+  st.iters[p] = 0;
+  st.J[p] = 0.0;
+  if (J_clear) J_clear[p] = 0.0;
+}
+
+#define PIFCM_DISPATCH_C(c, CALL)  \
+  switch (c) {                     \
+    case 2: { constexpr int C = 2; CALL; } \
+    case 3: { constexpr int C = 3; CALL; } \
+    case 4: { constexpr int C = 4; CALL; } \
+    case 5: { constexpr int C = 5; CALL; } \
+    case 6: { constexpr int C = 6; CALL; } \
+    case 7: { constexpr int C = 7; CALL; } \
+    case 8: { constexpr int C = 8; CALL; } \
+    default: return cudaErrorInvalidValue; \
+  }
+
+}  // namespace
+
+int plain_blocks(long long nvox, int vpt) {
+  const long long per = static_cast<long long>(PT) * vpt;
+  return static_cast<int>((nvox + per - 1) / per);
+}
+
+cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s) {
+  PIFCM_DISPATCH_C(c, (plain_kernel<C><<<blocks, PT, 0, s>>>(a)); return cudaGetLastError());
+}
+
+cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s) {
+  PIFCM_DISPATCH_C(c, (reduce_kernel<C><<<a.P, RT, 0, s>>>(a)); return cudaGetLastError());
+}
+
+cudaError_t launch_run_init(int c, int P, const double* c0, RunState st, double* J_clear,
+                            cudaStream_t s) {
+  const int b = (P + 127) / 128;
+  PIFCM_DISPATCH_C(c, (run_init_kernel<C><<<b, 128, 0, s>>>(P, c0, st, J_clear));
+                   return cudaGetLastError());
+}
+
+}  // namespace pifcm

@@ -159,3 +159,17 @@ def uneven_volumes(count=48, seed=3, lo=64, hi=224, sigmas=(0.03, 0.07, 0.12)):
                             bias=0.1, levels=levels, radii=radii)
         out.append((vol, c))
     return out
+
+
+def random_memberships(shape, c, seed=0, padded_pitch=None):
+    """Random positive memberships summing to 1 over the c clusters (inputs for
+    single-iteration tests), float32 of shape (c,) + shape; with
+    ``padded_pitch`` the x axis is zero-padded to that length."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((c,) + tuple(shape)) + 0.05
+    u = (u / u.sum(axis=0, keepdims=True)).astype(np.float32)
+    if padded_pitch is not None:
+        out = np.zeros((c,) + tuple(shape[:-1]) + (padded_pitch,), dtype=np.float32)
+        out[..., :shape[-1]] = u
+        return out
+    return u

@@ -1,0 +1,148 @@
+"""The C ABI library loads, exports every symbol include/pifcm.h declares, and
+rejects bad arguments on the host before any CUDA call (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_01981_gb300 import build, native
+    build.build()
+    return native.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "pifcm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = _declared_functions()
+    for n in ("ifcm_fit", "pso_fitness_batch", "pso_step", "pso_init", "ifcm_normalize",
+              "pifcm3d", "pifcm3d_host"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2002_01981_gb300 import native
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in native.SIGNATURES, name
+
+
+def test_struct_sizes_match_the_header_layout():
+    from paper_2002_01981_gb300 import native as N
+    assert ctypes.sizeof(N.IfcmShape) == 16
+    assert ctypes.sizeof(N.IfcmParams) == 56
+    assert ctypes.sizeof(N.PsoState) == 64
+    assert ctypes.sizeof(N.PifcmOptions) == 40
+    assert ctypes.sizeof(N.PifcmResult) == 8 * 8 + 4 * 8 + 8 + 4 * 4
+
+
+def _params(**kw):
+    from paper_2002_01981_gb300 import native as N
+    d = dict(c=4, m=2.0, V=1, h=1.0, max_iter=50, eps_u=1e-5, dist_floor=1e-12)
+    d.update(kw)
+    return N.IfcmParams(d["c"], d["m"], d["V"], d["h"], d["max_iter"], d["eps_u"],
+                        d["dist_floor"])
+
+
+@pytest.mark.parametrize("shape,ok", [((181, 217, 181, 184), True), ((5, 1, 1, 8), True),
+                                      ((5, 4, 3, 6), False), ((0, 4, 3, 4), False),
+                                      ((5, 4, 3, 4), False), ((5, 4, -1, 8), False)])
+def test_shape_validation(lib, shape, ok):
+    from paper_2002_01981_gb300 import native as N
+    nx, ny, nz, pitch = shape
+    shp = N.IfcmShape(nx, ny, nz, pitch)
+    fake = ctypes.c_void_p(256)          # never dereferenced: checks fail first
+    st = lib.ifcm_normalize(fake, fake, shp, fake, 0, None)
+    if ok:
+        assert st == 2          # passes the checks, then: workspace of 0 bytes
+    else:
+        assert st == 1
+        assert lib.ifcm_last_error()
+
+
+@pytest.mark.parametrize("kw,status", [(dict(c=1), 1), (dict(c=9), 1), (dict(m=1.0), 1),
+                                       (dict(m=float("nan")), 1), (dict(V=2), 6),
+                                       (dict(max_iter=0), 1), (dict(eps_u=-1.0), 1),
+                                       (dict(dist_floor=0.0), 1)])
+def test_parameter_validation(lib, kw, status):
+    from paper_2002_01981_gb300 import native as N
+    shp = N.IfcmShape(8, 8, 8, 8)
+    p = _params(**kw)
+    fake = ctypes.c_void_p(256)
+    st = lib.ifcm_fit(fake, shp, ctypes.byref(p), fake, None, None, None, None, None, None,
+                      fake, 1 << 40, None)
+    assert st == status
+
+
+def test_misaligned_and_null_pointers(lib):
+    from paper_2002_01981_gb300 import native as N
+    shp = N.IfcmShape(8, 8, 8, 8)
+    p = _params()
+    st = lib.ifcm_fit(ctypes.c_void_p(260), shp, ctypes.byref(p), ctypes.c_void_p(256), None,
+                      None, None, None, None, None, ctypes.c_void_p(256), 1 << 40, None)
+    assert st == 1 and b"aligned" in lib.ifcm_last_error()
+    st = lib.pso_fitness_batch(ctypes.c_void_p(256), shp, ctypes.byref(p), None, 4,
+                               ctypes.c_void_p(256), None, None, None, None,
+                               ctypes.c_void_p(256), 1 << 40, None)
+    assert st == 1
+    st = lib.pso_fitness_batch(ctypes.c_void_p(256), shp, ctypes.byref(p), ctypes.c_void_p(256),
+                               0, ctypes.c_void_p(256), ctypes.c_void_p(256),
+                               ctypes.c_void_p(256), None, None, ctypes.c_void_p(256), 1 << 40,
+                               None)
+    assert st == 1
+
+
+def test_swarm_validation(lib):
+    from paper_2002_01981_gb300 import native as N
+    s = N.PsoState(0, 1, 0.2, 1, 256, 256, 256, 256, 256)
+    assert lib.pso_init(ctypes.byref(s), None) == 1
+    s = N.PsoState(4, 1, 0.0, 1, 256, 256, 256, 256, 256)
+    assert lib.pso_step(ctypes.byref(s), ctypes.c_void_p(256), None) == 1
+    s = N.PsoState(4, -1, 0.2, 1, 256, 256, 256, 256, 256)
+    assert lib.pso_init(ctypes.byref(s), None) == 1
+    s = N.PsoState(2000, 1, 0.2, 1, 256, 256, 256, 256, 256)
+    assert lib.pso_init(ctypes.byref(s), None) == 1
+
+
+def test_workspace_sizes_scale_with_the_batch(lib):
+    from paper_2002_01981_gb300 import native as N
+    shp = N.IfcmShape(181, 217, 181, 184)
+    p = _params()
+    one = lib.pso_fitness_batch_workspace_bytes(shp, ctypes.byref(p), 1)
+    twenty = lib.pso_fitness_batch_workspace_bytes(shp, ctypes.byref(p), 20)
+    plane = 184 * 217 * 181 * 4
+    # two membership buffers of c planes per particle dominate
+    assert twenty - one >= 19 * 2 * 4 * plane
+    assert twenty < 21 * (2 * 4 * plane) + (1 << 26)
+    o = N.PifcmOptions(20, 30, 1, 0.2, 1, 300, -1)
+    full = lib.pifcm3d_workspace_bytes(shp, ctypes.byref(p), ctypes.byref(o))
+    assert full >= twenty
+    host = lib.pifcm3d_host_workspace_bytes(shp, ctypes.byref(p), ctypes.byref(o))
+    assert host >= full + 5 * plane
+    assert lib.ifcm_fit_workspace_bytes(shp, ctypes.byref(_params(c=9))) == 0
+
+
+def test_options_validation(lib):
+    from paper_2002_01981_gb300 import native as N
+    shp = N.IfcmShape(8, 8, 8, 8)
+    p = _params()
+    fake = ctypes.c_void_p(256)
+    for o in (N.PifcmOptions(0, 3, 1, 0.2, 1, 300, -1), N.PifcmOptions(4, 0, 1, 0.2, 1, 300, -1),
+              N.PifcmOptions(4, 3, 1, 0.2, 1, 300, 8), N.PifcmOptions(4, 3, 1, -0.2, 1, 300, -1)):
+        assert lib.pifcm3d(fake, shp, ctypes.byref(p), ctypes.byref(o), None, fake, fake,
+                           1 << 40, None) == 1
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.ifcm_status_string(s)

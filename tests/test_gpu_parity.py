@@ -1,0 +1,279 @@
+"""GPU (C ABI) vs FP64 oracle, element by element, on seeded inputs.
+
+Tolerances: memberships <= 1e-5 max-abs (FP32 path), centres <= 1e-6
+relative, J <= 1e-5 relative, hard labels identical on >= 99.99% of voxels.
+Iteration counts are fixed (eps = 0) wherever a stop decision could fall on
+either side of the threshold in FP32 vs FP64.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ifcm as O          # noqa: E402
+from oracle import pso as OP          # noqa: E402
+from paper_2002_01981_gb300 import phantoms  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-5
+C_RTOL = 1e-6
+J_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_01981_gb300 import build
+    build.build()
+    from paper_2002_01981_gb300 import ifcm
+    return ifcm
+
+
+def dev_vol(a):
+    """(nz, ny, nx) float32 -> padded CUDA tensor (nz, ny, pitch)."""
+    return torch.from_numpy(phantoms.pad_pitch(np.asarray(a, np.float32))).cuda()
+
+
+def dev_u(u):
+    """(c, nz, ny, nx) float32 -> padded CUDA tensor."""
+    c, nz, ny, nx = u.shape
+    out = np.zeros((c, nz, ny, phantoms.pitch_for(nx)), np.float32)
+    out[..., :nx] = u
+    return torch.from_numpy(out).cuda()
+
+
+def unpad(t, nx):
+    return t[..., :nx].cpu().numpy().astype(np.float64)
+
+
+def unit_volume(shape, seed, sigma=0.06):
+    """Seeded phantom already inside [0, 1] (input of the fit entry points)."""
+    raw = phantoms.brain_phantom(shape, seed=seed, sigma=sigma)
+    return np.clip(raw, 0.0, 1.0).astype(np.float32)
+
+
+def labels_agree(Ug, Uo):
+    return np.mean(np.argmax(Ug, 0) == np.argmax(Uo, 0))
+
+
+# ------------------------------------------------------------ normalise
+@pytest.mark.parametrize("shape", [(7, 13, 29), (1, 64, 64), (3, 1, 5), (33, 41, 37)])
+def test_normalize_matches_oracle(G, shape):
+    raw = phantoms.brain_phantom(shape, seed=3) * 3.7 - 0.4
+    raw = raw.astype(np.float32)
+    x = G.ifcm_normalize(dev_vol(raw), nx=shape[2])
+    ref = O.normalize(raw)
+    got = unpad(x, shape[2])
+    assert np.max(np.abs(got - ref)) <= 2.0 ** -23
+    assert got.min() == 0.0 and got.max() == 1.0
+
+
+def test_normalize_flags_constant_and_nonfinite(G):
+    from paper_2002_01981_gb300.native import IfcmError
+    with pytest.raises(IfcmError):
+        G.ifcm_normalize(dev_vol(np.full((4, 5, 6), 0.3, np.float32)), nx=6)
+    bad = np.random.default_rng(0).random((4, 5, 6)).astype(np.float32)
+    bad[2, 3, 1] = np.nan
+    with pytest.raises(IfcmError):
+        G.ifcm_normalize(dev_vol(bad), nx=6)
+
+
+# ----------------------------------------------------- one IFCM iteration
+CASES_ONE = [
+    # shape (nz, ny, nx), c, m, lambda, xi
+    ((9, 14, 21), 4, 2.0, 0.4, 0.3),
+    ((5, 17, 70), 3, 2.0, 0.8, 0.6),      # three x tiles, ragged
+    ((40, 9, 33), 4, 2.0, 0.5, 0.5),      # two z-chunks, ragged
+    ((1, 37, 45), 4, 2.0, 0.7, 0.2),      # 2D: 8-neighbourhood
+    ((3, 3, 3), 2, 2.0, 0.9, 0.9),
+    ((2, 2, 2), 5, 2.0, 0.3, 0.6),
+    ((1, 1, 7), 3, 2.0, 0.5, 0.5),        # a line
+    ((1, 1, 1), 2, 2.0, 0.5, 0.5),        # no neighbours: H = F = 0
+    ((6, 11, 13), 8, 2.0, 0.6, 0.4),
+    ((6, 11, 13), 6, 1.5, 0.6, 0.4),      # general m
+    ((4, 10, 12), 4, 3.0, 0.2, 0.7),
+    ((7, 12, 10), 4, 2.0, 0.0, 0.0),      # plain FCM step
+]
+
+
+@pytest.mark.parametrize("shape,c,m,lam,xi", CASES_ONE)
+def test_one_iteration(G, shape, c, m, lam, xi):
+    x = unit_volume(shape, seed=11)
+    U = phantoms.random_memberships(shape, c, seed=12)
+    C = np.linspace(0.1, 0.9, c)
+    prm = G.Params(c=c, m=m, max_iter=1, eps_u=0.0)
+    Ug, Cg, Jg, itg = G.ifcm_fit(dev_vol(x), prm, (lam, xi), nx=shape[2], u_init=dev_u(U),
+                                 c_init=C)
+    Uo, Co, Jo, ito = O.ifcm_fit(x.astype(np.float64), U.astype(np.float64), C, lam, xi, m, 1,
+                                 0.0)
+    assert itg == ito == 1
+    assert np.max(np.abs(unpad(Ug, shape[2]) - Uo)) <= U_TOL
+    assert np.allclose(Cg.cpu().numpy(), Co, rtol=C_RTOL, atol=0)
+    assert abs(Jg - Jo) <= J_RTOL * abs(Jo)
+
+
+def test_flat_neighbourhoods(G):
+    # noise-free piecewise-constant volume: many voxels have sum_k g_ik = 0
+    x = phantoms.piecewise_cube(6, levels=(0.1, 0.5, 0.9), nz=5)
+    U = phantoms.random_memberships(x.shape, 3, seed=4)
+    C = np.array([0.2, 0.5, 0.8])
+    prm = G.Params(c=3, max_iter=1, eps_u=0.0)
+    Ug, Cg, Jg, _ = G.ifcm_fit(dev_vol(x), prm, (0.6, 0.3), nx=6, u_init=dev_u(U), c_init=C)
+    Uo, Co, Jo, _ = O.ifcm_fit(x.astype(np.float64), U.astype(np.float64), C, 0.6, 0.3, 2.0, 1,
+                               0.0)
+    assert np.max(np.abs(unpad(Ug, 6) - Uo)) <= U_TOL
+    assert np.allclose(Cg.cpu().numpy(), Co, rtol=C_RTOL)
+
+
+# --------------------------------------------------------- whole runs
+@pytest.mark.parametrize("shape,c,lam,xi,iters", [((12, 20, 36), 4, 0.5, 0.4, 20),
+                                                  ((1, 64, 64), 4, 0.7, 0.3, 30),
+                                                  ((21, 18, 40), 3, 0.9, 0.8, 25)])
+def test_fixed_iteration_runs(G, shape, c, lam, xi, iters):
+    x = unit_volume(shape, seed=21)
+    U = phantoms.random_memberships(shape, c, seed=22)
+    C = np.linspace(0.15, 0.85, c)
+    prm = G.Params(c=c, max_iter=iters, eps_u=0.0)
+    Ug, Cg, Jg, itg = G.ifcm_fit(dev_vol(x), prm, (lam, xi), nx=shape[2], u_init=dev_u(U),
+                                 c_init=C)
+    Uo, Co, Jo, ito = O.ifcm_fit(x.astype(np.float64), U.astype(np.float64), C, lam, xi, 2.0,
+                                 iters, 0.0)
+    Ugn = unpad(Ug, shape[2])
+    assert itg == ito == iters
+    assert np.max(np.abs(Ugn - Uo)) <= U_TOL
+    assert np.allclose(Cg.cpu().numpy(), Co, rtol=C_RTOL)
+    assert abs(Jg - Jo) <= J_RTOL * abs(Jo)
+    assert labels_agree(Ugn, Uo) >= 0.9999
+
+
+def test_plain_form_matches_oracle(G):
+    shape = (10, 16, 23)
+    x = unit_volume(shape, seed=31)
+    U = phantoms.random_memberships(shape, 4, seed=32)
+    C = np.linspace(0.1, 0.9, 4)
+    prm = G.Params(c=4, max_iter=12, eps_u=0.0)
+    Ug, Cg, Jg, itg = G.ifcm_fit(dev_vol(x), prm, (0.6, 0.5), nx=shape[2], u_init=dev_u(U),
+                                 c_init=C, plain=True)
+    Uo, Co, Jo, ito = O.ifcm_fit(x.astype(np.float64), U.astype(np.float64), C, 0.6, 0.5, 2.0,
+                                 12, 0.0)
+    assert itg == ito
+    assert np.max(np.abs(unpad(Ug, shape[2]) - Uo)) <= U_TOL
+    assert np.allclose(Cg.cpu().numpy(), Co, rtol=C_RTOL)
+
+
+def test_fcm_start_and_stop_rule(G):
+    shape = (1, 48, 52)
+    raw = phantoms.ellipse_slice(64, seed=1)[:, :48, :52]
+    x = O.normalize(raw)
+    xg = G.ifcm_normalize(dev_vol(raw), nx=52)
+    prm = G.Params(c=4, max_iter=300, eps_u=1e-5)
+    Ug, Cg, Jg, itg = G.ifcm_fit(xg, prm, (0.0, 0.0), nx=52)
+    Uo, Co, Jo, ito = O.fcm_init(x, 4, 2.0, 300, 1e-5)
+    # the stop test is taken in FP32 on the GPU and FP64 in the oracle
+    assert abs(itg - ito) <= 1
+    assert np.max(np.abs(unpad(Ug, 52) - Uo)) <= 1e-4
+    assert np.allclose(Cg.cpu().numpy(), Co, rtol=1e-5)
+
+
+# ------------------------------------------------------- particle batch
+def test_fitness_batch_matches_independent_runs(G):
+    shape = (14, 22, 30)
+    x = unit_volume(shape, seed=41)
+    U0 = phantoms.random_memberships(shape, 4, seed=42)
+    C0 = np.array([0.05, 0.3, 0.55, 0.85])
+    lam_xi = np.random.default_rng(43).random((7, 2))
+    prm = G.Params(c=4, max_iter=15, eps_u=0.0)
+    fit, its, cout = G.pso_fitness_batch(dev_vol(x), prm, lam_xi, dev_u(U0), C0, nx=shape[2],
+                                         want_centres=True)
+    fit, its, cout = fit.cpu().numpy(), its.cpu().numpy(), cout.cpu().numpy()
+    for p in range(7):
+        _, Co, Jo, ito = O.ifcm_fit(x.astype(np.float64), U0.astype(np.float64), C0,
+                                    lam_xi[p, 0], lam_xi[p, 1], 2.0, 15, 0.0)
+        assert its[p] == ito
+        assert abs(fit[p] - Jo) <= J_RTOL * abs(Jo)
+        assert np.allclose(cout[p], Co, rtol=C_RTOL)
+
+
+def test_fitness_batch_with_stop_rule(G):
+    shape = (8, 16, 20)
+    x = unit_volume(shape, seed=51)
+    xo = x.astype(np.float64)
+    U0o, C0o, _, _ = O.fcm_init(xo, 4)
+    xg = dev_vol(x)
+    U0g, C0g, _, _ = G.ifcm_fit(xg, G.Params(c=4, max_iter=300, eps_u=1e-5), (0.0, 0.0),
+                                nx=shape[2])
+    lam_xi = np.random.default_rng(52).random((5, 2))
+    prm = G.Params(c=4, max_iter=50, eps_u=1e-5)
+    fit, its, _ = G.pso_fitness_batch(xg, prm, lam_xi, U0g, C0g, nx=shape[2])
+    fit, its = fit.cpu().numpy(), its.cpu().numpy()
+    for p in range(5):
+        _, _, Jo, ito = O.ifcm_fit(xo, U0o, C0o, lam_xi[p, 0], lam_xi[p, 1], 2.0, 50, 1e-5)
+        assert abs(int(its[p]) - ito) <= 1
+        assert abs(fit[p] - Jo) <= 1e-4 * abs(Jo)
+
+
+# ------------------------------------------------------------- swarm
+@pytest.mark.parametrize("P,radius,seed", [(1, 1, 3), (2, 1, 4), (3, 0, 5), (20, 1, 6),
+                                           (64, 2, 7), (10, 1, 2**40 + 17)])
+def test_swarm_is_bit_identical(G, P, radius, seed):
+    sw = G.Swarm(P, seed=seed, radius=radius, vmax=0.2).init()
+    ref = OP.Swarm(P, seed=seed, vmax=0.2, radius=radius)
+    assert np.array_equal(sw.x.cpu().numpy(), ref.x)
+    assert np.array_equal(sw.v.cpu().numpy(), ref.v)
+    rng = np.random.default_rng(seed % 1000)
+    for g in range(12):
+        f = rng.random(P)
+        if g == 5:
+            f[:] = 0.25          # ties everywhere
+        sw.step(torch.tensor(f, device="cuda"))
+        OP.pso_step(ref, f)
+        assert np.array_equal(sw.x.cpu().numpy(), ref.x)
+        assert np.array_equal(sw.v.cpu().numpy(), ref.v)
+        assert np.array_equal(sw.pbest_x.cpu().numpy(), ref.pbest_x)
+        assert np.array_equal(sw.pbest_f.cpu().numpy(), ref.pbest_f)
+    assert int(sw.gen.item()) == ref.gen
+
+
+# ------------------------------------------------------------ Algorithm 1
+def test_pifcm3d_small_run_matches_oracle(G):
+    raw = phantoms.ellipse_slice(24, seed=1, sigma=0.05)
+    prm = G.Params(c=4, max_iter=8, eps_u=0.0)
+    opts = G.Options(P=4, generations=3, seed=9, init_max_iter=40)
+    U, res = G.pifcm3d(dev_vol(raw), prm, opts, nx=24)
+    ref = OP.pifcm3d(raw, c=4, P=4, generations=3, seed=9, max_iter=8, eps=0.0,
+                     init_max_iter=40)
+    assert res["status"] == 0
+    # each swarm is driven by its own fitness values; they agree unless a
+    # personal-best comparison is a near tie (none expected at these sizes)
+    assert res["lambda"] == ref["lambda"] and res["xi"] == ref["xi"]
+    assert np.max(np.abs(unpad(U, 24) - ref["U"])) <= U_TOL
+    assert np.allclose(res["centres"], ref["C"], rtol=1e-5)
+    assert abs(res["J"] - ref["J"]) <= J_RTOL * abs(ref["J"])
+    assert res["iters_final"] == ref["iters"]
+    assert abs(res["best_fitness"] - ref["pbest_f"].min()) <= J_RTOL * ref["pbest_f"].min()
+
+
+def test_pifcm3d_host_equals_device(G):
+    raw = phantoms.brain_phantom((10, 12, 14), seed=5)
+    vol = phantoms.pad_pitch(raw)
+    prm = G.Params(c=4, max_iter=6, eps_u=0.0)
+    opts = G.Options(P=3, generations=2, seed=2, init_max_iter=30)
+    Ud, rd = G.pifcm3d(torch.from_numpy(vol).cuda(), prm, opts, nx=14)
+    uh = torch.empty((4,) + vol.shape, dtype=torch.float32).pin_memory()
+    _, rh = G.pifcm3d_host(torch.from_numpy(vol).pin_memory(), prm, opts, nx=14, u_out=uh)
+    assert rd == rh
+    assert torch.equal(Ud.cpu()[..., :14], uh[..., :14])
+
+
+def test_pifcm3d_slice_mode(G):
+    raw = phantoms.brain_phantom((6, 20, 22), seed=8)
+    prm = G.Params(c=3, max_iter=5, eps_u=0.0)
+    opts = G.Options(P=3, generations=2, seed=4, init_max_iter=30, slice_z=2)
+    U, res = G.pifcm3d(dev_vol(raw), prm, opts, nx=22)
+    ref = OP.pifcm3d(raw, c=3, P=3, generations=2, seed=4, max_iter=5, eps=0.0,
+                     init_max_iter=30, z=2)
+    assert U.shape[1] == 1
+    assert res["lambda"] == ref["lambda"]
+    assert np.max(np.abs(unpad(U, 22) - ref["U"])) <= U_TOL
