@@ -1,0 +1,341 @@
+"""Benchmark of the 3DPIFCM hot path on GB300: IFCM voxel x particle x
+iteration updates per second for whole Algorithm 1 runs.
+
+One step = one complete 3DPIFCM run (Algorithm 1 / Algorithm 2) on the
+181x217x181 brain stand-in: min-max normalisation, the FCM start, 30 swarm
+generations of 20 particles (each particle one IFCM run of <= 50 iterations
+stopping at max|du| < 1e-5, all particles batched), the swarm updates and the
+final IFCM run at the best particle.  Inputs are resident in HBM before the
+timed region; the per-step membership buffers (4.6 GB) exceed the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own volume (seed + rank): independent
+problems, weak scaling, no data-path collective; timings are reduced with a
+MAX over ranks.  ``--impl reference`` times the FP64 oracle on the host cores
+(bounded samples of the same workload).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IFCM voxel·particle·iter updates/s (batched vs plain), % of HBM roofline"
+UNIT = "updates/s"
+SHAPE = (181, 217, 181)            # (nz, ny, nx)
+C, M = 4, 2.0
+P, GENERATIONS, MAX_ITER, EPS = 20, 30, 50, 1e-5
+INIT_MAX_ITER = 300
+SEED = 2
+WORKLOAD = ("brain stand-in 181x217x181 (nested ellipsoids 0/0.25/0.55/0.85, +-10% bias, "
+            "Rician sigma 0.07), c=4, m=2, 26-neighbourhood, 20 particles x 30 generations, "
+            "<=50 IFCM iterations per fitness, stop max|du|<1e-5")
+CPU_SLAB = 48                      # z-planes of the oracle's bounded sample
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ helpers
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def stencil_source_sha():
+    h = hashlib.sha256()
+    for name in ("ifcm_stencil.cu", "ifcm_math.cuh", "common.cuh", "launch.h"):
+        with open(os.path.join(ROOT, "paper_2002_01981_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stencil_traffic_per_update():
+    """DRAM bytes per update of the stencil kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha") == stencil_source_sha():
+            return float(d["dram_bytes_per_update"])
+    except Exception:
+        pass
+    return None
+
+
+def launches_per_run(init_iters_launched, generations, max_iter):
+    # normalise (2) + FCM start (2 per iteration + copy) + swarm init
+    # + per generation (state init + 2 per iteration + swarm step)
+    # + best + final run (state init + 2 per iteration + copy) + result
+    return (2 + 2 * init_iters_launched + 1 + 1 + generations * (1 + 2 * max_iter + 1) + 1 +
+            (1 + 2 * max_iter + 1) + 1)
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample_rate(raw, seconds_cap=30.0):
+    """Updates/s of the FP64 oracle: IFCM iterations of one particle
+    (lambda = xi = 0.5) on a 48-plane z-slab of the workload volume."""
+    from oracle import ifcm as O
+    x = O.normalize(raw)[:CPU_SLAB]
+    U = np.full((C,) + x.shape, 1.0 / C)
+    Cc = (np.arange(C) + 0.5) / C
+    U, Cc, _, _ = O.ifcm_iteration(x, U, Cc, 0.0, 0.0)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        U, Cc, _, _ = O.ifcm_iteration(x, U, Cc, 0.5, 0.5)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_cap / 3 or n >= 3:
+            break
+    return n * x.size / el, n, el, x.shape
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2002_01981_gb300 import phantoms
+    from oracle import ifcm as O
+    raw = phantoms.brain_phantom(SHAPE, seed=SEED, sigma=0.07)
+    x = O.normalize(raw)[:CPU_SLAB]
+    U = np.full((C,) + x.shape, 1.0 / C)
+    Cc = (np.arange(C) + 0.5) / C
+    U, Cc, _, _ = O.ifcm_iteration(x, U, Cc, 0.0, 0.0)
+    for _ in range(args.warmup):
+        U, Cc, _, _ = O.ifcm_iteration(x, U, Cc, 0.5, 0.5)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, Cc, _, _ = O.ifcm_iteration(x, U, Cc, 0.5, 0.5)
+    el = time.perf_counter() - t0
+    value = args.steps * x.size / el
+    sample = (f"one FP64 oracle IFCM iteration (one particle, lambda=xi=0.5) per step on a "
+              f"{CPU_SLAB}-plane z-slab (181x217x{CPU_SLAB}) of the workload volume")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_01981_gb300 import ifcm as G
+    from paper_2002_01981_gb300 import phantoms
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    raw = phantoms.brain_phantom(SHAPE, seed=SEED + rank, sigma=0.07)
+    nz, ny, nx = SHAPE
+    vol_host = torch.from_numpy(phantoms.pad_pitch(raw)).pin_memory()
+    vol = vol_host.to(dev)
+    prm = G.Params(c=C, m=M, max_iter=MAX_ITER, eps_u=EPS)
+    opts = G.Options(P=P, generations=GENERATIONS, seed=SEED + rank, init_max_iter=INIT_MAX_ITER)
+    bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
+    N = nx * ny * nz
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs, sync=False)
+    barrier()
+    _, first = G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs)
+    if first["status"]:
+        raise RuntimeError(f"device status {first['status']}")
+
+    # ---- timed region (device-resident inputs)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    G.profile_read()                    # drop anything recorded so far
+    G.profile_enable(True)
+    barrier()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs, sync=False)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    G.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    kernel_ms, kernel_launches = G.profile_read()
+    _, res = G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs)   # same work every step
+    updates_step = res["updates"]
+    init_updates = res["iters_init"] * N
+    stencil_updates_step = updates_step - init_updates
+
+    t = torch.tensor([ms, float(updates_step * args.steps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        t[0] = tmax[0]
+    ms_max, total_updates = float(t[0]), float(t[1])
+    value = total_updates / (ms_max / 1e3)
+
+    # ---- end to end through the host entry point (copies inside the region)
+    u_host = torch.empty((C, nz, ny, vol.shape[2]), dtype=torch.float32).pin_memory()
+    ws_host = G.pifcm3d_host_workspace(G.shape_of(vol, nx), prm, opts)
+    del bufs
+    G.pifcm3d_host(vol_host, prm, opts, nx=nx, u_out=u_host, ws=ws_host)   # warm
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        _, rh = G.pifcm3d_host(vol_host, prm, opts, nx=nx, u_out=u_host, ws=ws_host)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps * rh["updates"] / float(te[0])
+
+    # ---- roofline of the stencil kernel (dominant kernel)
+    hbm, peak_kind = peaks()
+    bytes_per_update = 2 * C * 4 + 4           # U^t read + U^{t+1} write + x (one particle per tile)
+    per_launch_updates = stencil_updates_step * args.steps / max(kernel_launches, 1)
+    achieved = (stencil_updates_step * args.steps * bytes_per_update) / (kernel_ms / 1e3) / 1e9
+    traffic_pu = stencil_traffic_per_update()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": traffic_pu * per_launch_updates if traffic_pu else None,
+                "algorithmic_bytes_per_launch": per_launch_updates * bytes_per_update,
+                "kernel": "stencil_kernel<4>", "kernel_ms_total": kernel_ms,
+                "kernel_launches": kernel_launches,
+                "kernel_share_of_step": kernel_ms / ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one whole Algorithm 1 run",
+                       "updates_per_step": updates_step,
+                       "fcm_start_updates_per_step": init_updates,
+                       "l2": "inputs larger than L2 (4.6 GB of membership buffers per step)",
+                       "parallelism": f"independent volume per GPU x{world}"},
+            "roofline": roofline, "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(vol_host.numel() * 4),
+                    "d2h_bytes_per_step": int(u_host.numel() * 4 + 120)},
+            "gpu_launches": args.steps * launches_per_run(INIT_MAX_ITER, GENERATIONS, MAX_ITER)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el, shp = oracle_sample_rate(raw)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} FP64 oracle IFCM iterations of one particle "
+                                          f"on a {shp[0]}x{shp[1]}x{shp[2]} z-slab, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
