@@ -215,6 +215,27 @@ ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_par
                          void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * ifcm_fit without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * run a segmentation (a graph being recorded under global capture mode, a
+ * plugin whose host framework owns every allocation and hands it only its
+ * input and output pointers, a loop that must not take the allocator's
+ * implicit synchronisation).  Arguments and results are those of ifcm_fit;
+ * the scratch is a 64 MiB array held by the library on every GPU that loads
+ * it, until the process exits.  Calls whose ifcm_fit workspace would exceed
+ * 64 MiB (about 1.36 million voxels at c = 4, e.g. 111^3) return IFCM_ERR_NOMEM with a
+ * message naming both sizes.  The first call on each device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call on a device shares the one array: calls that overlap on the GPU
+ * (other streams, other threads) race and corrupt each other's results, so
+ * serialise them.  No call allocates or frees device memory.
+ */
+ifcm_status ifcm_fit_noalloc(const float* x, ifcm_shape shape, const ifcm_params* p,
+                             const double* lam_xi, const float* u_init, const double* c_init,
+                             float* u_out, double* c_out, double* J_out, int32_t* iters_out,
+                             void* stream);
+
+/* ---------------------------------------------------------------------------
  * Profiling counters (host side, per process): when enabled, the library
  * records CUDA events around every launch of the stencil-iteration kernel
  * and the updates it was launched for; ifcm_profile_read() synchronises the

@@ -446,6 +446,17 @@ ifcm_status check_options(const pifcm_options* o, const ifcm_shape& s) {
 
 }  // namespace
 
+namespace pifcm {
+// Sets the thread-local message ifcm_last_error() returns (for entry points
+// defined in other translation units).
+void set_error_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+}  // namespace pifcm
+
 // ============================================================== C ABI
 extern "C" {
 

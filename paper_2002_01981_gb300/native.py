@@ -74,6 +74,9 @@ SIGNATURES = {
     "pifcm3d_host": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams),
                                POINTER(PifcmOptions), c_void_p, POINTER(PifcmResult),
                                c_void_p, c_size_t, c_void_p]),
+    "ifcm_fit_noalloc": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p]),
     "ifcm_profile_enable": (None, [c_int32]),
     "ifcm_profile_read": (c_int32, [POINTER(c_double), POINTER(c_int64)]),
 }
