@@ -222,8 +222,11 @@ def run_ours(args):
     nz, ny, nx = SHAPE
     vol_host = torch.from_numpy(phantoms.pad_pitch(raw)).pin_memory()
     vol = vol_host.to(dev)
-    prm = G.Params(c=C, m=M, max_iter=MAX_ITER, eps_u=EPS)
-    opts = G.Options(P=P, generations=GENERATIONS, seed=SEED + rank, init_max_iter=INIT_MAX_ITER)
+    n_p, n_gen, n_it, n_init = P, GENERATIONS, MAX_ITER, INIT_MAX_ITER
+    if args.small:       # short case for profiler captures: same volume and kernels
+        n_p, n_gen, n_it, n_init = 4, 1, 3, 3
+    prm = G.Params(c=C, m=M, max_iter=n_it, eps_u=EPS)
+    opts = G.Options(P=n_p, generations=n_gen, seed=SEED + rank, init_max_iter=n_init)
     bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
     N = nx * ny * nz
 
@@ -266,6 +269,15 @@ def run_ours(args):
         t[0] = tmax[0]
     ms_max, total_updates = float(t[0]), float(t[1])
     value = total_updates / (ms_max / 1e3)
+
+    if args.small:
+        if rank == 0:
+            print(json.dumps({"small_case": True, "ms_per_step": ms_max / args.steps,
+                              "updates_per_step": updates_step, "kernel_ms": kernel_ms,
+                              "kernel_launches": kernel_launches}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
 
     # ---- end to end through the host entry point (copies inside the region)
     u_host = torch.empty((C, nz, ny, vol.shape[2]), dtype=torch.float32).pin_memory()
@@ -331,6 +343,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: 4 particles x 1 generation x 3 iterations")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -66,6 +66,16 @@ ifcm_status check_params(const ifcm_params* p) {
   return IFCM_OK;
 }
 
+// The kernels index one particle's c membership planes with 32-bit offsets.
+ifcm_status check_extent(const ifcm_shape& s, const ifcm_params* p) {
+  const double elems = static_cast<double>(p->c) * s.pitch_x * s.ny * s.nz;
+  if (elems >= 2147483647.0)
+    return fail(IFCM_ERR_INVALID,
+                "c * pitch_x * ny * nz = %.0f must stay below 2^31 (memberships of one run)",
+                elems);
+  return IFCM_OK;
+}
+
 ifcm_status check_aligned(const void* ptr, const char* what) {
   if (!ptr) return fail(IFCM_ERR_INVALID, "%s is NULL", what);
   if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0)
@@ -179,7 +189,7 @@ ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int
                      int box_planes) {
   ST_TRY(get_encode());
   const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * 4;
-  if (planes <= 0) {   // 3D volume map
+  if (planes <= 0) {   // 3D volume map: positions outside the volume read as NaN
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
                           static_cast<cuuint64_t>(s.nz)};
     cuuint64_t strides[2] = {row, row * s.ny};
@@ -188,7 +198,7 @@ ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
     if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (volume) failed: %d", (int)r);
     return IFCM_OK;
   }
@@ -294,7 +304,8 @@ ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* 
   r.nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
   r.status = status;
 
-  const long long items = static_cast<long long>(P) * t.n_tiles;
+  const int npi = stencil_particles_per_item(c);
+  const long long items = static_cast<long long>((P + npi - 1) / npi) * t.n_tiles;
   long long grid = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c);
   if (grid > items) grid = items;
 
@@ -532,6 +543,7 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
                      size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  ST_TRY(check_extent(shape, p));
   ST_TRY(check_aligned(x, "x"));
   ST_TRY(check_aligned(ws, "ws"));
   if (!lam_xi) return fail(IFCM_ERR_INVALID, "lam_xi is NULL");
@@ -565,6 +577,7 @@ ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* 
                            size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  ST_TRY(check_extent(shape, p));
   ST_TRY(check_aligned(x, "x"));
   ST_TRY(check_aligned(ws, "ws"));
   if (u_out) ST_TRY(check_aligned(u_out, "u_out"));
@@ -601,6 +614,7 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
                               double* c_out, void* ws, size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  ST_TRY(check_extent(shape, p));
   if (P < 1 || P > kMaxP) return fail(IFCM_ERR_INVALID, "P = %d outside 1..%d", P, kMaxP);
   ST_TRY(check_aligned(x, "x"));
   ST_TRY(check_aligned(u0, "u0"));
@@ -655,6 +669,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
                     size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  ST_TRY(check_extent(shape, p));
   ST_TRY(check_options(o, shape));
   ST_TRY(check_aligned(vol, "vol"));
   ST_TRY(check_aligned(ws, "ws"));
@@ -731,6 +746,7 @@ ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_par
                          void* ws, size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  ST_TRY(check_extent(shape, p));
   ST_TRY(check_options(o, shape));
   ST_TRY(check_aligned(ws, "ws"));
   if (!vol_host || !result_host) return fail(IFCM_ERR_INVALID, "vol_host / result_host is NULL");

@@ -35,6 +35,7 @@ struct StencilArgs {
   DevStatus* status;
 };
 
+int stencil_particles_per_item(int c);   // particles sharing one work item
 size_t stencil_smem_bytes(int c);
 int stencil_blocks_per_sm(int c);
 cudaError_t launch_stencil(int c, const CUtensorMap& tm_x, const CUtensorMap& tm_u,
