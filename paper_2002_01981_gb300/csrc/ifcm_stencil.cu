@@ -9,12 +9,14 @@
 // (one-voxel halo in y, aligned four-voxel margins in x) into a ring of
 // shared-memory stages, gated by "full" (transaction bytes) and "empty"
 // (one arrival per consumer warp) mbarriers.  Warps 0-7 are consumers: thread
-// (tx, ty) owns column (x0 + tx, y0 + ty) and keeps three centres of the column
+// (tx, ty) owns column (x0 + tx, y0 + ty) and keeps four centres of the column
 // in registers.  The plane being consumed contributes to the centre below it
-// (dz = +1), its own centre (dz = 0) and the centre above (dz = -1); the three
-// register sets rotate roles from plane to plane (the loop is unrolled by
-// three), so nothing is copied.  A plane's stage is released only after the
-// next plane has been consumed, because the centre it holds is finalised then:
+// (dz = +1), its own centre (dz = 0) and the centre above (dz = -1); the
+// centre two planes below, completed by the previous plane, is finalised in
+// the same step so that its long dependency chain overlaps the stencil
+// arithmetic.  The per-centre sums are float2 pairs (the two particles of an
+// item, or two clusters) updated with packed FP32x2 instructions.  A plane's
+// stage is released once the centre it holds has been finalised:
 // H = sum u g / sum g, F = sum u^2 q^2 / sum q^2 (q^2 = dx^2+dy^2+dz^2,
 // reading R1), Eqs 4 and 2, U^{t+1} written from registers, and the centre's
 // shares of sum u^m, sum u^m x, J and max|du|.
@@ -42,10 +44,10 @@ constexpr int BX = TX + 8;             // x box: 4-voxel aligned margins (TMA x 
 constexpr int BY = TY + 2;             // y box: one-voxel halo
 constexpr int PLANE = BX * BY;         // floats in one channel of a stage
 #ifndef PIFCM_STENCIL_STAGES
-#define PIFCM_STENCIL_STAGES 5
+#define PIFCM_STENCIL_STAGES 8
 #endif
-constexpr int NSTAGE = PIFCM_STENCIL_STAGES;   // ring depth (>= 4: prev, current, next + 1 in flight)
-static_assert(NSTAGE >= 4, "the consumers hold three stages at a time");
+constexpr int NSTAGE = PIFCM_STENCIL_STAGES;   // ring depth
+static_assert(NSTAGE >= 5, "the consumers hold four stages at a time (pz-2 .. pz+1)");
 constexpr int XBYTES = ((PLANE * 4 + 127) / 128) * 128;
 constexpr int CBAR = 1;                // named barrier id of the consumer warps
 
@@ -128,42 +130,85 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const int* act
   return it;
 }
 
+// The per-centre sums are kept as float2 pairs and updated with packed FP32x2
+// instructions (half the issue slots of scalar FP32).  With two particles per
+// item, pair k holds cluster k of particle 0 and of particle 1; with one, pair
+// k holds clusters 2k and 2k+1 (the second half of the last pair is unused
+// when c is odd).
+template <int C, int NP>
+struct Pairs {
+  static constexpr int K = NP == 2 ? C : (C + 1) / 2;
+};
+
+template <int C, int NP>
+__device__ __forceinline__ float2 load_pair(const float* __restrict__ us, int k, int off) {
+  if (NP == 2) return make_float2(us[k * PLANE + off], us[ufloats<C>() + k * PLANE + off]);
+  const float lo = us[(2 * k) * PLANE + off];
+  const float hi = (2 * k + 1 < C) ? us[(2 * k + 1) * PLANE + off] : 0.0f;
+  return make_float2(lo, hi);
+}
+
+// Component of (particle p, cluster j) in an array of pairs.
+template <int C, int NP>
+__device__ __forceinline__ float pick(const float2 (&v)[Pairs<C, NP>::K], int p, int j) {
+  if (NP == 2) return p == 0 ? v[j].x : v[j].y;
+  return (j & 1) ? v[j >> 1].y : v[j >> 1].x;
+}
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 // Accumulators of one centre voxel of the column, for NP particles.
 template <int C, int NP>
 struct Slot {
+  static constexpr int K = Pairs<C, NP>::K;
   float G;            // sum_k g_ik (shared by the particles)
-  float H[NP][C];     // sum_k u_kj g_ik
-  float F[NP][C];     // sum_k u_kj^2 q^2_ik
+  float2 H[K];        // sum_k u_kj g_ik
+  float2 F[K];        // sum_k u_kj^2 q^2_ik
   __device__ __forceinline__ void clear() {
     G = 0.0f;
 #pragma unroll
-    for (int p = 0; p < NP; ++p)
-#pragma unroll
-      for (int j = 0; j < C; ++j) H[p][j] = F[p][j] = 0.0f;
+    for (int k = 0; k < K; ++k) H[k] = F[k] = make_float2(0.0f, 0.0f);
   }
 };
 
+// A thread's shares of the item's sums: sum u^m and sum u^m x (paired like the
+// slots), J and max|du| per particle.
 template <int C, int NP>
 struct Sums {
-  float s0[NP][C], s1[NP][C], J[NP], dm[NP];
+  static constexpr int K = Pairs<C, NP>::K;
+  float2 s0[K], s1[K];
+  float J[NP], dm[NP];
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
+    for (int k = 0; k < K; ++k) s0[k] = s1[k] = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int j = 0; j < C; ++j) s0[p][j] = s1[p][j] = 0.0f;
-      J[p] = dm[p] = 0.0f;
-    }
+    for (int p = 0; p < NP; ++p) J[p] = dm[p] = 0.0f;
   }
+};
+
+// Constants of the item being processed, shared by the consumer threads.
+template <int C, int NP>
+struct ItemConst {
+  float2 ncc[Pairs<C, NP>::K];   // minus the centres C^t, paired like the slots
+  float2 nlam, nxi;              // minus lambda and xi of the pair's particles
+  float* dst[NP];                // each particle's U^{t+1}
 };
 
 // Contributions of one plane (x in xs, memberships of particle p at us + p *
-// ufloats<C>()) to the centres below (lo), in (mid) and above (hi) it.
+// ufloats<C>()) to the centres below (lo), in (mid) and above (hi) it.  F uses
+// the plane's window sums A = sum w and B = sum (dx^2 + dy^2) w (w = u^2): the
+// planes above and below weigh q^2 = 1 + dx^2 + dy^2 (A + B), the same plane
+// dx^2 + dy^2 (B).
 template <int C, int NP, bool Z3>
 __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
                                                  const float* __restrict__ us, int cidx,
                                                  float x_lo, float x_mid, float x_hi,
                                                  Slot<C, NP>& lo, Slot<C, NP>& mid,
                                                  Slot<C, NP>& hi) {
+  constexpr int K = Pairs<C, NP>::K;
+  float2 A[K], B[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) A[k] = B[k] = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
@@ -172,8 +217,6 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
       const float xk = xs[off];
       const bool self = (dx == 0 && dy == 0);
       const int q2 = dx * dx + dy * dy;          // folded after unrolling
-      const float qm = static_cast<float>(q2);    // weight in the same plane
-      const float qa = static_cast<float>(q2 + 1);  // weight in the planes above / below
       float gl = 0.0f, gh = 0.0f, gm = 0.0f;
       if (Z3) {
         gl = gdist(x_lo, xk);
@@ -185,45 +228,54 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
         gm = gdist(x_mid, xk);
         mid.G += gm;
       }
+      const float2 gl2 = dup2(gl), gh2 = dup2(gh), gm2 = dup2(gm);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const float uk = us[p * ufloats<C>() + j * PLANE + off];
-          const float wk = uk * uk;
-          if (Z3) {
-            lo.H[p][j] = fmaf(uk, gl, lo.H[p][j]);
-            hi.H[p][j] = fmaf(uk, gh, hi.H[p][j]);
-            lo.F[p][j] = fmaf(qa, wk, lo.F[p][j]);
-            hi.F[p][j] = fmaf(qa, wk, hi.F[p][j]);
-          }
-          if (!self) {
-            mid.H[p][j] = fmaf(uk, gm, mid.H[p][j]);
-            mid.F[p][j] = fmaf(qm, wk, mid.F[p][j]);
-          }
+      for (int k = 0; k < K; ++k) {
+        const float2 uk = load_pair<C, NP>(us, k, off);
+        if (Z3) {
+          lo.H[k] = __ffma2_rn(uk, gl2, lo.H[k]);
+          hi.H[k] = __ffma2_rn(uk, gh2, hi.H[k]);
         }
+        if (!self) mid.H[k] = __ffma2_rn(uk, gm2, mid.H[k]);
+        const float2 wk = __fmul2_rn(uk, uk);
+        A[k] = __fadd2_rn(A[k], wk);
+        if (q2 == 1) B[k] = __fadd2_rn(B[k], wk);
+        if (q2 == 2) B[k] = __ffma2_rn(dup2(2.0f), wk, B[k]);
       }
     }
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (Z3) {
+      const float2 ab = __fadd2_rn(A[k], B[k]);
+      lo.F[k] = __fadd2_rn(lo.F[k], ab);
+      hi.F[k] = __fadd2_rn(hi.F[k], ab);
+    }
+    mid.F[k] = __fadd2_rn(mid.F[k], B[k]);
+  }
 }
 
-// Per-item constants of one consumer thread.
-template <int C, int NP>
+// Per-item position of one consumer thread's column.
 struct Ctx {
   int X, Y;
   bool col_ok, col_interior;
   int col_off;                 // Y * pitch + X
-  float lam[NP], xi[NP], cc[NP][C];
-  float* dst[NP];              // particle's U^{t+1} base
 };
 
-// Finalise one centre (its u^t is read from its plane's stage at cus).
+__device__ __forceinline__ float2 max2(float2 v, float lo) {
+  return make_float2(fmaxf(v.x, lo), fmaxf(v.y, lo));
+}
+
+// Finalise one centre (its u^t is read from its plane's stage at cus): H and F
+// (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
+// the centre's shares of Eqs 1 and 3, in packed pairs.
 template <int C, int NP>
 __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
                                                 int cidx, float xc, int z, bool interior,
                                                 const StencilArgs& a, const Item& it,
-                                                const Ctx<C, NP>& cx, const MethodConsts& k,
-                                                Sums<C, NP>& acc) {
+                                                const ItemConst<C, NP>& ic, const Ctx& cx,
+                                                const MethodConsts& k, Sums<C, NP>& acc) {
+  constexpr int K = Pairs<C, NP>::K;
   float invQ;
   int cnt = 1;
   if (interior) {
@@ -233,46 +285,131 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
     box_counts(cx.X, cx.Y, z, a.nx, a.ny, a.nz, cnt, Q);
     invQ = cnt > 0 ? __frcp_rn(Q) : 0.0f;
   }
-  const bool normal_g = sl.G >= 1.0e-30f;
-  const float invG = normal_g ? fast_rcp(sl.G) : 0.0f;
-  const int plane = a.nz * a.ny * a.pitch;              // < 2^31 / c (host-checked)
+  float2 H[K], F[K];
+  if (cnt == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) H[q] = F[q] = make_float2(0.0f, 0.0f);
+  } else {
+    const float2 iq = dup2(invQ);
+#pragma unroll
+    for (int q = 0; q < K; ++q) F[q] = __fmul2_rn(sl.F[q], iq);
+    if (sl.G >= 1.0e-30f) {
+      const float2 ig = dup2(fast_rcp(sl.G));
+#pragma unroll
+      for (int q = 0; q < K; ++q) H[q] = __fmul2_rn(sl.H[q], ig);
+    } else if (sl.G > 0.0f) {
+      const float2 ig = dup2(__frcp_rn(sl.G));
+#pragma unroll
+      for (int q = 0; q < K; ++q) H[q] = __fmul2_rn(sl.H[q], ig);
+    } else {   // every neighbour equals x_i: plain mean of u_kj (reading R3)
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int pid = p == 0 ? it.p0 : it.p1;
+        float Hm[C];
+        flat_neighbourhood_mean<C>(a.u_src + static_cast<long long>(pid) * a.src_pstride, cx.X,
+                                   cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          if (NP == 2) {
+            if (p == 0) H[j].x = Hm[j];
+            else H[j].y = Hm[j];
+          } else if (j & 1) {
+            H[j >> 1].y = Hm[j];
+          } else {
+            H[j >> 1].x = Hm[j];
+            if (j == C - 1) H[j >> 1].y = 0.0f;
+          }
+        }
+      }
+    }
+  }
+  // Eq 4 with reading R2
+  const float2 one2 = dup2(1.0f), xc2 = dup2(xc);
+  float2 d2[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const float2 fac =
+        max2(__ffma2_rn(ic.nxi, F[q], __ffma2_rn(ic.nlam, H[q], one2)), 0.0f);
+    const float2 dd = __fadd2_rn(xc2, ic.ncc[q]);
+    d2[q] = max2(__fmul2_rn(__fmul2_rn(dd, dd), fac), k.dist_floor);
+  }
+  // Eq 2
+  float2 u[K], um[K];
+  if (k.m_is_2) {
+    float2 r[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) r[q] = make_float2(fast_rcp(d2[q].x), fast_rcp(d2[q].y));
+    float2 inv;
+    if (NP == 2) {
+      float2 S = r[0];
+#pragma unroll
+      for (int q = 1; q < K; ++q) S = __fadd2_rn(S, r[q]);
+      inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
+      acc.J[0] += inv.x;                       // sum_j u_j^2 d2_j = 1/S
+      acc.J[NP - 1] += inv.y;
+    } else {
+      float S = 0.0f;
+#pragma unroll
+      for (int q = 0; q < K; ++q) S += (2 * q + 1 < C) ? r[q].x + r[q].y : r[q].x;
+      inv = dup2(fast_rcp(S));
+      acc.J[0] += inv.x;
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      u[q] = __fmul2_rn(r[q], inv);
+      um[q] = __fmul2_rn(u[q], u[q]);
+    }
+  } else {
+    float Sp[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Sp[p] = 0.0f;
+    float av[NP][C];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        av[p][j] = exp2f(-k.inv_m1 * log2f(pick<C, NP>(d2, p, j)));
+        Sp[p] += av[p][j];
+      }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float invS = fast_rcp(Sp[p]);
+      float Jv = 0.0f;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float uj = av[p][j] * invS;
+        const float umj = exp2f(k.m * log2f(uj));
+        Jv += umj * pick<C, NP>(d2, p, j);
+        if (NP == 2) {
+          if (p == 0) { u[j].x = uj; um[j].x = umj; }
+          else { u[j].y = uj; um[j].y = umj; }
+        } else if (j & 1) {
+          u[j >> 1].y = uj; um[j >> 1].y = umj;
+        } else {
+          u[j >> 1].x = uj; um[j >> 1].x = umj;
+          if (j == C - 1) { u[j >> 1].y = 0.0f; um[j >> 1].y = 0.0f; }
+        }
+      }
+      acc.J[p] += Jv;
+    }
+  }
+  // Eq 3 shares, max|du|, and the store of U^{t+1}
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    acc.s0[q] = __fadd2_rn(acc.s0[q], um[q]);
+    acc.s1[q] = __ffma2_rn(um[q], xc2, acc.s1[q]);
+  }
+  const int plane = a.nz * a.ny * a.pitch;              // c * plane < 2^31 (host-checked)
   const int voff = z * (a.ny * a.pitch) + cx.col_off;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     if (p == 1 && !it.two) break;
-    float H[C], F[C];
-    if (cnt == 0) {
-#pragma unroll
-      for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
-    } else {
-#pragma unroll
-      for (int j = 0; j < C; ++j) F[j] = sl.F[p][j] * invQ;
-      if (normal_g) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) H[j] = sl.H[p][j] * invG;
-      } else if (sl.G > 0.0f) {
-        const float r = __frcp_rn(sl.G);
-#pragma unroll
-        for (int j = 0; j < C; ++j) H[j] = sl.H[p][j] * r;
-      } else {
-        const int pid = p == 0 ? it.p0 : it.p1;
-        flat_neighbourhood_mean<C>(a.u_src + static_cast<long long>(pid) * a.src_pstride, cx.X,
-                                   cx.Y, z, a.nx, a.ny, a.nz, a.pitch, H);
-      }
-    }
-    MethodConsts kp = k;
-    kp.lam = cx.lam[p];
-    kp.xi = cx.xi[p];
-    float u[C], um[C], Jv;
-    voxel_update_fast<C>(H, F, xc, cx.cc[p], kp, u, um, Jv);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      cx.dst[p][j * plane + voff] = u[j];
-      acc.s0[p][j] += um[j];
-      acc.s1[p][j] = fmaf(um[j], xc, acc.s1[p][j]);
-      acc.dm[p] = fmaxf(acc.dm[p], fabsf(u[j] - cus[p * ufloats<C>() + j * PLANE + cidx]));
+      const float uj = pick<C, NP>(u, p, j);
+      ic.dst[p][j * plane + voff] = uj;
+      acc.dm[p] = fmaxf(acc.dm[p], fabsf(uj - cus[p * ufloats<C>() + j * PLANE + cidx]));
     }
-    acc.J[p] += Jv;
   }
 }
 
@@ -287,6 +424,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   __shared__ int s_nact;
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
+  __shared__ ItemConst<C, NP> s_ic;
 
   unsigned char* dsmem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -376,21 +514,32 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
 
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const Item it = decode_item<NP>(a, s_act, nact, w);
-    Ctx<C, NP> cx;
+    Ctx cx;
     cx.X = it.x0 + tx;
     cx.Y = it.y0 + ty;
     cx.col_ok = (cx.X < a.nx) && (cx.Y < a.ny);
     cx.col_interior = cx.X > 0 && cx.X < a.nx - 1 && cx.Y > 0 && cx.Y < a.ny - 1;
     cx.col_off = cx.Y * a.pitch + cx.X;
+    if (tid == 0) {
+      float lam[2], xi[2], cc[2][C];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const int pid = p == 0 ? it.p0 : it.p1;
-      cx.lam[p] = static_cast<float>(a.lam_xi[2 * pid]);
-      cx.xi[p] = static_cast<float>(a.lam_xi[2 * pid + 1]);
+      for (int p = 0; p < 2; ++p) {
+        const int pid = (p == 0 || NP == 1) ? it.p0 : it.p1;
+        lam[p] = static_cast<float>(a.lam_xi[2 * pid]);
+        xi[p] = static_cast<float>(a.lam_xi[2 * pid + 1]);
 #pragma unroll
-      for (int j = 0; j < C; ++j) cx.cc[p][j] = static_cast<float>(a.centres[pid * C + j]);
-      cx.dst[p] = a.u_dst + static_cast<size_t>(pid) * C * plane;
+        for (int j = 0; j < C; ++j) cc[p][j] = static_cast<float>(a.centres[pid * C + j]);
+        if (p < NP) s_ic.dst[p] = a.u_dst + static_cast<size_t>(pid) * C * plane;
+      }
+      s_ic.nlam = make_float2(-lam[0], -lam[1]);
+      s_ic.nxi = make_float2(-xi[0], -xi[1]);
+#pragma unroll
+      for (int q = 0; q < Pairs<C, NP>::K; ++q) {
+        if (NP == 2) s_ic.ncc[q] = make_float2(-cc[0][q], -cc[1][q]);
+        else s_ic.ncc[q] = make_float2(-cc[0][2 * q], 2 * q + 1 < C ? -cc[0][2 * q + 1] : 0.0f);
+      }
     }
+    consumer_sync();
     Slot<C, NP> s0, s1, s2;
     s0.clear();
     s1.clear();
@@ -400,8 +549,16 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     const int np = it.pze - it.pzb + 1;
     const int q0 = q;
 
-    // One plane step with roles (lo, mid, hi).
-    auto step = [&](int kk, Slot<C, NP>& lo, Slot<C, NP>& mid, Slot<C, NP>& hi) {
+    // Delayed finalisation: the centre completed by plane pz - 1 is finalised
+    // while plane pz accumulates, in one basic block, so that the long
+    // dependency chain of Eqs 4 and 2 overlaps the stencil arithmetic.
+    // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1.
+    Slot<C, NP>& sd = s0;
+    Slot<C, NP>& sl = s1;
+    Slot<C, NP>& sm = s2;
+    Slot<C, NP> sh;
+    sh.clear();
+    for (int kk = 0; kk < np; ++kk) {
       const int qq = q0 + kk;
       const int pz = it.pzb + kk;
       const bool has_next = kk + 1 < np;
@@ -412,29 +569,42 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         const float x_mid = xs[cidx];
         const float x_lo = kk > 0 ? xs_of((qq + NSTAGE - 1) % NSTAGE)[cidx] : 0.0f;
         const float x_hi = has_next ? xs_of((qq + 1) % NSTAGE)[cidx] : 0.0f;
-        if (z3)
-          accumulate_plane<C, NP, true>(xs, us, cidx, x_lo, x_mid, x_hi, lo, mid, hi);
-        else
-          accumulate_plane<C, NP, false>(xs, us, cidx, x_lo, x_mid, x_hi, lo, mid, hi);
-        if (cx.col_ok) {
-          if (pz - 1 >= it.z0 && pz - 1 < it.z1)   // the centre below is complete
-            finalize_centre<C, NP>(lo, us_of((qq + NSTAGE - 1) % NSTAGE), cidx, x_lo, pz - 1,
-                                   cx.col_interior && pz - 1 > 0 && pz - 1 < a.nz - 1, a, it,
-                                   cx, k, acc);
-          if (pz == a.nz - 1 && pz >= it.z0 && pz < it.z1)   // last plane of the volume
-            finalize_centre<C, NP>(mid, us, cidx, x_mid, pz, cx.col_interior && !z3, a, it,
-                                   cx, k, acc);
+        const int zd = pz - 2;
+        if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
+          const int sdi = (qq + NSTAGE - 2) % NSTAGE;
+          finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
+                                 cx.col_interior && zd > 0 && zd < a.nz - 1, a, it, s_ic, cx, k,
+                                 acc);
         }
+        if (z3)
+          accumulate_plane<C, NP, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+        else
+          accumulate_plane<C, NP, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
       }
-      if (kk > 0) release(qq - 1);         // the plane below is no longer needed
-      if (kk + 1 == np) release(qq);       // last plane of the item
-      lo.clear();                          // becomes the next step's "hi"
-    };
-
-    for (int kk = 0; kk < np; kk += 3) {
-      step(kk, s0, s1, s2);
-      if (kk + 1 < np) step(kk + 1, s1, s2, s0);
-      if (kk + 2 < np) step(kk + 2, s2, s0, s1);
+      if (kk >= 2) release(qq - 2);
+      sd = sl;
+      sl = sm;
+      sm = sh;
+      sh.clear();
+    }
+    // After the last plane: sd = centre pze - 1 (complete) and sl = centre pze
+    // (complete only when pze is the last plane of the volume).
+    {
+      const int ql = q0 + np - 1;
+      const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
+      if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
+        const int sdi = (ql + NSTAGE - 1) % NSTAGE;
+        finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
+                               cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < a.nz - 1, a,
+                               it, s_ic, cx, k, acc);
+      }
+      if (live && it.pze == a.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
+        const int sli = ql % NSTAGE;
+        finalize_centre<C, NP>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
+                               cx.col_interior && !z3, a, it, s_ic, cx, k, acc);
+      }
+      if (np >= 2) release(ql - 1);
+      release(ql);
     }
     q = q0 + np;
 
@@ -443,8 +613,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     for (int p = 0; p < NP; ++p) {
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const float v0 = warp_sum(acc.s0[p][j]);
-        const float v1 = warp_sum(acc.s1[p][j]);
+        const float v0 = warp_sum(pick<C, NP>(acc.s0, p, j));
+        const float v1 = warp_sum(pick<C, NP>(acc.s1, p, j));
         if (lane == 0) {
           s_red[warp][p * (2 * C + 2) + j] = v0;
           s_red[warp][p * (2 * C + 2) + C + j] = v1;
@@ -480,6 +650,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   }
 }
 
+// ---------------------------------------------------------------------------
 template <int C, int NP>
 cudaError_t launch_c(const CUtensorMap& tm_x, const CUtensorMap& tm_u, const StencilArgs& a,
                      int grid, cudaStream_t s) {
@@ -493,10 +664,10 @@ cudaError_t launch_c(const CUtensorMap& tm_x, const CUtensorMap& tm_u, const Ste
 
 template <int C, int NP>
 int blocks_per_sm_c() {
+  int n = 0;
   constexpr int smem = smem_total<C, NP>();
   cudaFuncSetAttribute(stencil_kernel<C, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem);
-  int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP>, NT, smem) !=
       cudaSuccess)
     return 1;
