@@ -41,6 +41,7 @@ WORKLOAD = ("brain stand-in 181x217x181 (nested ellipsoids 0/0.25/0.55/0.85, +-1
             "Rician sigma 0.07), c=4, m=2, 26-neighbourhood, 20 particles x 30 generations, "
             "<=50 IFCM iterations per fitness, stop max|du|<1e-5")
 CPU_SLAB = 48                      # z-planes of the oracle's bounded sample
+PARTICLES_PER_ITEM = 2             # particles sharing one stencil work item at c = 4
 
 
 def peaks():
@@ -142,6 +143,32 @@ def launches_per_run(init_iters_launched, generations, max_iter):
     # + best + final run (state init + 2 per iteration + copy) + result
     return (2 + 2 * init_iters_launched + 1 + 1 + generations * (1 + 2 * max_iter + 1) + 1 +
             (1 + 2 * max_iter + 1) + 1)
+
+
+def plain_form_rate(G, vol, nx, prm, opts, stream, particles=2):
+    """Updates/s of the plain comparison form on the same volume and
+    parameters: the FCM start, then `particles` IFCM runs one after another,
+    each one particle per launch with the host checking convergence after
+    every iteration (the shape of the paper's Algorithm 2)."""
+    import torch
+    x = G.ifcm_normalize(vol, nx=nx)
+    U0, C0, _, _ = G.ifcm_fit(x, G.Params(c=prm.c, m=prm.m, max_iter=opts.init_max_iter,
+                                          eps_u=prm.eps_u), (0.0, 0.0), nx=nx, plain=True)
+    lam_xi = [(0.5, 0.3), (0.8, 0.6), (0.2, 0.7), (0.6, 0.1)][:particles]
+    N = int(x.shape[0]) * int(x.shape[1]) * nx
+    G.ifcm_fit(x, G.Params(c=prm.c, m=prm.m, max_iter=2, eps_u=0.0), lam_xi[0], nx=nx,
+               u_init=U0, c_init=C0, plain=True)                       # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = 0
+    for lx in lam_xi:
+        _, _, _, it = G.ifcm_fit(x, prm, lx, nx=nx, u_init=U0, c_init=C0, plain=True)
+        iters += it
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": iters * N / el, "unit": UNIT, "iterations": iters,
+            "sample": f"{particles} particles, one IFCM run each (<= {prm.max_iter} iterations, "
+                      f"host stop test per iteration), plain kernel, same volume"}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -279,6 +306,10 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    # ---- the plain form (paper's Algorithm 2 shape): one particle per launch,
+    # one thread per voxel reading neighbours from global memory, host loop
+    plain = plain_form_rate(G, vol, nx, prm, opts, stream) if rank == 0 else None
+
     # ---- end to end through the host entry point (copies inside the region)
     u_host = torch.empty((C, nz, ny, vol.shape[2]), dtype=torch.float32).pin_memory()
     ws_host = G.pifcm3d_host_workspace(G.shape_of(vol, nx), prm, opts)
@@ -298,7 +329,8 @@ def run_ours(args):
 
     # ---- roofline of the stencil kernel (dominant kernel)
     hbm, peak_kind = peaks()
-    bytes_per_update = 2 * C * 4 + 4           # U^t read + U^{t+1} write + x (one particle per tile)
+    # U^t read + U^{t+1} write + x read once per item, shared by the item's particles
+    bytes_per_update = 2 * C * 4 + 4.0 / PARTICLES_PER_ITEM
     per_launch_updates = stencil_updates_step * args.steps / max(kernel_launches, 1)
     achieved = (stencil_updates_step * args.steps * bytes_per_update) / (kernel_ms / 1e3) / 1e9
     traffic_pu = stencil_traffic_per_update()
@@ -324,6 +356,9 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(vol_host.numel() * 4),
                     "d2h_bytes_per_step": int(u_host.numel() * 4 + 120)},
             "gpu_launches": args.steps * launches_per_run(INIT_MAX_ITER, GENERATIONS, MAX_ITER)}
+    if plain is not None:
+        line["plain"] = plain
+        line["plain"]["batched_over_plain"] = value / world / plain["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, el, shp = oracle_sample_rate(raw)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
