@@ -115,6 +115,25 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_over_ranks(dist, world, seconds, updates, device):
+    """Whole-job figures over the ranks (one process per GPU, each on its own
+    volume): the slowest rank's seconds and the sum of all ranks' updates.
+    Used only for measurement; no membership data crosses ranks."""
+    if world == 1:
+        return float(seconds), float(updates)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def rank_seed(rank):
+    """Seed of rank r's phantom and swarm: independent problems per GPU."""
+    return SEED + rank
+
+
 def stencil_source_sha():
     h = hashlib.sha256()
     for name in ("ifcm_stencil.cu", "ifcm_math.cuh", "common.cuh", "launch.h"):
@@ -245,7 +264,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    raw = phantoms.brain_phantom(SHAPE, seed=SEED + rank, sigma=0.07)
+    raw = phantoms.brain_phantom(SHAPE, seed=rank_seed(rank), sigma=0.07)
     nz, ny, nx = SHAPE
     vol_host = torch.from_numpy(phantoms.pad_pitch(raw)).pin_memory()
     vol = vol_host.to(dev)
@@ -253,7 +272,7 @@ def run_ours(args):
     if args.small:       # short case for profiler captures: same volume and kernels
         n_p, n_gen, n_it, n_init = 4, 1, 3, 3
     prm = G.Params(c=C, m=M, max_iter=n_it, eps_u=EPS)
-    opts = G.Options(P=n_p, generations=n_gen, seed=SEED + rank, init_max_iter=n_init)
+    opts = G.Options(P=n_p, generations=n_gen, seed=rank_seed(rank), init_max_iter=n_init)
     bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
     N = nx * ny * nz
 
@@ -288,14 +307,10 @@ def run_ours(args):
     init_updates = res["iters_init"] * N
     stencil_updates_step = updates_step - init_updates
 
-    t = torch.tensor([ms, float(updates_step * args.steps)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        t[0] = tmax[0]
-    ms_max, total_updates = float(t[0]), float(t[1])
-    value = total_updates / (ms_max / 1e3)
+    s_max, total_updates = reduce_over_ranks(dist, world, ms / 1e3, updates_step * args.steps,
+                                             dev)
+    ms_max = s_max * 1e3
+    value = total_updates / s_max
 
     if args.small:
         if rank == 0:
@@ -322,10 +337,8 @@ def run_ours(args):
         _, rh = G.pifcm3d_host(vol_host, prm, opts, nx=nx, u_out=u_host, ws=ws_host)
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps * rh["updates"] / float(te[0])
+    e2e_max, e2e_updates = reduce_over_ranks(dist, world, e2e_s, e2e_steps * rh["updates"], dev)
+    e2e_value = e2e_updates / e2e_max
 
     # ---- roofline of the stencil kernel (dominant kernel)
     hbm, peak_kind = peaks()
