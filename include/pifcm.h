@@ -175,6 +175,38 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
                               void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Algorithm 1 step 4 for many swarms at once: each volume brings its own
+ * particles, start (u0, c0) and cluster count, and every (volume, particle)
+ * fitness is evaluated in the same batched launches: volumes of the same c
+ * share each stencil launch (up to 64 volumes and 4096 particles per launch).
+ * Volumes are taken in order, grouped by c, and packed into waves that fit
+ * ws_bytes; a wave runs to completion before the next reuses the workspace.
+ * Results are identical to pso_fitness_batch on each volume alone.
+ * vols: HOST array of n descriptors (pointers inside are device memory).
+ * p: m, max_iter, eps_u, dist_floor and V are shared; p->c is ignored.
+ */
+typedef struct {
+  const float* x;            /* device, normalised volume [nz][ny][pitch_x]   */
+  ifcm_shape shape;
+  int32_t c;                 /* clusters of this volume, 2..8                 */
+  int32_t P;                 /* particles, >= 1                               */
+  const double* lam_xi;      /* device, P*2 (lambda, xi)                      */
+  const float* u0;           /* device [c][nz][ny][pitch_x]: shared start     */
+  const double* c0;          /* device, c: shared start                       */
+  double* fitness;           /* device, P                                     */
+  int32_t* iters;            /* device, P (may be NULL)                       */
+} ifcm_batch_volume;
+
+/* Workspace to run every volume of a c in one wave (the largest such group). */
+size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t n,
+                                         const ifcm_params* p);
+/* Smallest workspace that still runs (one volume per wave). */
+size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int32_t n,
+                                             const ifcm_params* p);
+ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Algorithm 1 step 3: x ~ U[0,1)^2, v ~ U[-vmax, vmax)^2, pbest_x = x,
  * pbest_f = +inf, gen = 0.  Draws are Philox4x32-10 keyed by seed with
  * counter (generation, particle, dimension, stream).

@@ -117,32 +117,61 @@ Tiling tiling(const ifcm_shape& s) {
 
 constexpr int kPlainVpt = 32;
 
-// Buffers of a batch of IFCM runs (P particles).
+// Buffers of a batch of IFCM runs over n volumes of the same c: two membership
+// buffers per volume (P particles each), the partial records of every
+// particle's tiles, and the per-particle run state (particle p of volume v is
+// state index pbase[v] + p).
 struct RunBufs {
-  float* ua;
-  float* ub;
+  int n;
+  float* ua[kMaxVols];
+  float* ub[kMaxVols];
+  int pbase[kMaxVols];
+  long long rec_base[kMaxVols];
+  int rec_per_particle[kMaxVols];
   double* partials;
   float* dmax;
   RunState st;
-  int n_rec;
 };
 
-RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P) {
-  RunBufs r;
-  const size_t pl = plane_elems(s);
-  r.ua = cv.take<float>(static_cast<size_t>(P) * c * pl);
-  r.ub = cv.take<float>(static_cast<size_t>(P) * c * pl);
-  const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
-  const int nrec_stencil = tiling(s).n_tiles;
-  const int nrec_plain = plain_blocks(nvox, kPlainVpt);
-  r.n_rec = nrec_stencil > nrec_plain ? nrec_stencil : nrec_plain;
-  r.partials = cv.take<double>(static_cast<size_t>(P) * r.n_rec * (2 * c + 1));
-  r.dmax = cv.take<float>(static_cast<size_t>(P) * r.n_rec);
-  r.st.centres = cv.take<double>(static_cast<size_t>(P) * c);
-  r.st.J = cv.take<double>(P);
-  r.st.active = cv.take<int32_t>(P);
-  r.st.iters = cv.take<int32_t>(P);
+RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, int c) {
+  RunBufs r{};
+  r.n = n;
+  long long recs = 0;
+  int pb = 0;
+  for (int v = 0; v < n; ++v) {
+    const size_t pl = plane_elems(shapes[v]);
+    r.ua[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
+    r.ub[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
+    const long long nvox = static_cast<long long>(shapes[v].nx) * shapes[v].ny * shapes[v].nz;
+    int nrec = tiling(shapes[v]).n_tiles;
+    const int nplain = plain_blocks(nvox, kPlainVpt);      // the plain kernel's records (P = 1)
+    if (nplain > nrec) nrec = nplain;
+    r.pbase[v] = pb;
+    r.rec_base[v] = recs;
+    r.rec_per_particle[v] = nrec;
+    recs += static_cast<long long>(P[v]) * nrec;
+    pb += P[v];
+  }
+  r.partials = cv.take<double>(static_cast<size_t>(recs) * (2 * c + 1));
+  r.dmax = cv.take<float>(static_cast<size_t>(recs));
+  r.st.centres = cv.take<double>(static_cast<size_t>(pb) * c);
+  r.st.J = cv.take<double>(pb);
+  r.st.active = cv.take<int32_t>(pb);
+  r.st.iters = cv.take<int32_t>(pb);
   r.st.updates = cv.take<unsigned long long>(1);
+  return r;
+}
+
+RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P) {
+  return carve_runs(cv, &s, &P, 1, c);
+}
+
+RunState shifted(const RunState& st, int pbase, int c) {
+  RunState r = st;
+  r.centres += static_cast<size_t>(pbase) * c;
+  r.J += pbase;
+  r.active += pbase;
+  r.iters += pbase;
   return r;
 }
 
@@ -247,82 +276,121 @@ cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out) {
 }
 
 // ------------------------------------------------------------ run loops
-ifcm_status fill_method(StencilArgs& a, const ifcm_params* p) {
+void fill_method(StencilArgs& a, const ifcm_params* p) {
   a.dist_floor = static_cast<float>(p->dist_floor);
   a.m = static_cast<float>(p->m);
   a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
   a.m_is_2 = p->m == 2.0;
-  return IFCM_OK;
 }
 
-// IFCM runs of P particles with the stencil kernel from the shared start
-// (u0 [c][plane], c0 [c] or NULL).
-ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* p,
-                        const double* lam_xi, int P, const float* u0, const double* c0,
-                        RunBufs& rb, double* fitness, int32_t* iters, double* c_out,
-                        DevStatus* status, cudaStream_t st) {
+// One volume of a batch of IFCM runs (host view).
+struct BatchVol {
+  const float* x;
+  ifcm_shape shape;
+  int P;
+  const double* lam_xi;   // device [P][2]
+  const float* u0;        // device [c][plane]: the shared start of the volume's runs
+  const double* c0;       // device [c] or NULL
+  double* fitness;        // device [P] or NULL
+  int32_t* iters;         // device [P] or NULL
+  double* c_out;          // device [P][c] or NULL
+};
+
+// IFCM runs of every particle of n volumes (same c, n <= kMaxVols) with the
+// stencil kernel: one launch per iteration covers all volumes' work items.
+ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p, RunBufs& rb,
+                              DevStatus* status, cudaStream_t st) {
   const int c = p->c;
-  const Tiling t = tiling(s);
-  const size_t pl = plane_elems(s);
-  CUtensorMap tm_x, tm_u0, tm_ua, tm_ub;
-  ST_TRY(make_map(&tm_x, x, s, 0, 0));
-  ST_TRY(make_map(&tm_u0, u0, s, c, c));
-  ST_TRY(make_map(&tm_ua, rb.ua, s, P * c, c));
-  ST_TRY(make_map(&tm_ub, rb.ub, s, P * c, c));
-  CU_TRY(launch_run_init(c, P, c0, rb.st, nullptr, st));
-
-  StencilArgs a{};
-  a.nx = s.nx;
-  a.ny = s.ny;
-  a.nz = s.nz;
-  a.pitch = s.pitch_x;
-  a.tiles_x = t.tiles_x;
-  a.tiles_y = t.tiles_y;
-  a.zchunks = t.zchunks;
-  a.tz = t.tz;
-  a.n_tiles = t.n_tiles;
-  a.P = P;
-  a.lam_xi = lam_xi;
-  a.centres = rb.st.centres;
-  a.active = rb.st.active;
-  a.partials = rb.partials;
-  a.dmax = rb.dmax;
-  a.status = status;
-  fill_method(a, p);
-
+  int P_total = 0;
+  long long items = 0;
+  const int npi = stencil_particles_per_item(c);
+  for (int v = 0; v < n; ++v) {
+    CU_TRY(launch_run_init(c, vols[v].P, vols[v].c0, shifted(rb.st, rb.pbase[v], c), nullptr,
+                           st));
+    P_total += vols[v].P;
+    items += static_cast<long long>((vols[v].P + npi - 1) / npi) * tiling(vols[v].shape).n_tiles;
+  }
+  // Three parameter blocks: iteration 0 (U0 -> ua), odd (ua -> ub), even (ub -> ua).
+  std::vector<StencilArgs> args(3);
+  for (int k = 0; k < 3; ++k) {
+    StencilArgs& a = args[k];
+    std::memset(static_cast<void*>(&a), 0, sizeof(StencilArgs));
+    a.n_vol = n;
+    a.centres = rb.st.centres;
+    a.active = rb.st.active;
+    a.partials = rb.partials;
+    a.dmax = rb.dmax;
+    a.status = status;
+    fill_method(a, p);
+    for (int v = 0; v < n; ++v) {
+      const BatchVol& bv = vols[v];
+      const ifcm_shape& s = bv.shape;
+      const Tiling t = tiling(s);
+      const size_t pl = plane_elems(s);
+      VolDesc& d = a.vol[v];
+      d.nx = s.nx;
+      d.ny = s.ny;
+      d.nz = s.nz;
+      d.pitch = s.pitch_x;
+      d.tiles_x = t.tiles_x;
+      d.tiles_y = t.tiles_y;
+      d.tz = t.tz;
+      d.n_tiles = t.n_tiles;
+      d.P = bv.P;
+      d.pbase = rb.pbase[v];
+      d.rec_base = rb.rec_base[v];
+      d.lam_xi = bv.lam_xi;
+      const float* src = k == 0 ? bv.u0 : (k == 1 ? rb.ua[v] : rb.ub[v]);
+      d.u_dst = k == 1 ? rb.ub[v] : rb.ua[v];
+      d.u_src = src;
+      d.src_pstride = k == 0 ? 0 : static_cast<long long>(c) * pl;
+      d.src_cstride = k == 0 ? 0 : c;
+      ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
+      ST_TRY(make_map(&a.tm_u[v], src, s, k == 0 ? c : bv.P * c, c));
+    }
+  }
   ReduceArgs r{};
-  r.P = P;
-  r.n_rec = t.n_tiles;
+  r.n_vol = n;
+  r.P_total = P_total;
   r.partials = rb.partials;
   r.dmax = rb.dmax;
   r.st = rb.st;
-  r.fitness = fitness;
-  r.iters_out = iters;
-  r.c_out = c_out;
   r.max_iter = p->max_iter;
   r.eps = p->eps_u;
-  r.nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
   r.status = status;
-
-  const int npi = stencil_particles_per_item(c);
-  const long long items = static_cast<long long>((P + npi - 1) / npi) * t.n_tiles;
+  for (int v = 0; v < n; ++v) {
+    ReduceVol& rv = r.vol[v];
+    rv.pbase = rb.pbase[v];
+    rv.P = vols[v].P;
+    rv.n_rec = tiling(vols[v].shape).n_tiles;
+    rv.rec_base = rb.rec_base[v];
+    rv.nvox = static_cast<long long>(vols[v].shape.nx) * vols[v].shape.ny * vols[v].shape.nz;
+    rv.fitness = vols[v].fitness;
+    rv.iters_out = vols[v].iters;
+    rv.c_out = vols[v].c_out;
+  }
   long long grid = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c);
   if (grid > items) grid = items;
+  if (grid < 1) grid = 1;
 
   for (int it = 0; it < p->max_iter; ++it) {
-    const bool first = it == 0;
-    a.u_dst = (it % 2 == 0) ? rb.ua : rb.ub;
-    a.u_src = first ? u0 : ((it % 2 == 1) ? rb.ua : rb.ub);
-    a.src_pstride = first ? 0 : static_cast<long long>(c) * pl;
-    a.src_cstride = first ? 0 : c;
-    const CUtensorMap& tm_u = first ? tm_u0 : ((it % 2 == 1) ? tm_ua : tm_ub);
+    const StencilArgs& a = args[it == 0 ? 0 : (it % 2 == 1 ? 1 : 2)];
     cudaEvent_t ev_end = nullptr;
     cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-    CU_TRY(launch_stencil(c, tm_x, tm_u, a, static_cast<int>(grid), st));
+    CU_TRY(launch_stencil(c, a, static_cast<int>(grid), st));
     if (ev_beg) cudaEventRecord(ev_end, st);
     CU_TRY(launch_reduce(c, r, st));
   }
   return IFCM_OK;
+}
+
+// The runs of P particles of one volume from the shared start (u0, c0).
+ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* p,
+                        const double* lam_xi, int P, const float* u0, const double* c0,
+                        RunBufs& rb, double* fitness, int32_t* iters, double* c_out,
+                        DevStatus* status, cudaStream_t st) {
+  BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out};
+  return run_stencil_batch(&bv, 1, p, rb, status, st);
 }
 
 // One run with the plain kernel (P = 1).  host_check: read max|du| after
@@ -357,21 +425,25 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   a.stencil = stencil ? 1 : 0;
   a.status = status;
   ReduceArgs r{};
-  r.P = 1;
-  r.n_rec = blocks;
+  r.n_vol = 1;
+  r.P_total = 1;
   r.partials = rb.partials;
   r.dmax = rb.dmax;
   r.st = rb.st;
-  r.fitness = J_out;
-  r.iters_out = iters_out;
-  r.c_out = c_out;
   r.max_iter = max_iter;
   r.eps = p->eps_u;
-  r.nvox = nvox;
   r.status = status;
+  r.vol[0].pbase = 0;
+  r.vol[0].P = 1;
+  r.vol[0].n_rec = blocks;
+  r.vol[0].rec_base = 0;
+  r.vol[0].nvox = nvox;
+  r.vol[0].fitness = J_out;
+  r.vol[0].iters_out = iters_out;
+  r.vol[0].c_out = c_out;
   for (int it = 0; it < max_iter; ++it) {
-    a.u_dst = (it % 2 == 0) ? rb.ua : rb.ub;
-    a.u_src = it == 0 ? u_init : ((it % 2 == 1) ? rb.ua : rb.ub);
+    a.u_dst = (it % 2 == 0) ? rb.ua[0] : rb.ub[0];
+    a.u_src = it == 0 ? u_init : ((it % 2 == 1) ? rb.ua[0] : rb.ub[0]);
     CU_TRY(launch_plain(c, a, blocks, st));
     CU_TRY(launch_reduce(c, r, st));
     if (host_check) {
@@ -566,7 +638,7 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
   ST_TRY(run_stencil(x, shape, p, lam_xi, 1, start, c_init, rb, J_out, iters_out, c_out, status,
                      st));
   if (u_out)
-    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out,
+    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out,
                               static_cast<long long>(p->c) * plane_elems(shape), st));
   return IFCM_OK;
 }
@@ -594,7 +666,7 @@ ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* 
                    true, u_init, c_init, p->max_iter, rb, iters_out, c_out, J_out, status,
                    true, st));
   if (u_out)
-    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out,
+    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out,
                               static_cast<long long>(p->c) * plane_elems(shape), st));
   return IFCM_OK;
 }
@@ -631,6 +703,137 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   return run_stencil(x, shape, p, lam_xi, P, u0, c0, rb, fitness, iters, c_out, status, st);
 }
+
+}  // extern "C"
+
+// -------------------------------------------------- pso_fitness_multi
+namespace {
+
+size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c) {
+  ifcm_shape shapes[kMaxVols];
+  int P[kMaxVols];
+  for (int i = 0; i < n; ++i) {
+    shapes[i] = vols[idx[i]].shape;
+    P[i] = vols[idx[i]].P;
+  }
+  Carver cv(nullptr);
+  carve_status(cv);
+  carve_runs(cv, shapes, P, n, c);
+  return cv.off + 256;
+}
+
+ifcm_status check_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p) {
+  if (!vols || n < 1) return fail(IFCM_ERR_INVALID, "need at least one volume");
+  if (!p) return fail(IFCM_ERR_INVALID, "params is NULL");
+  for (int i = 0; i < n; ++i) {
+    const ifcm_batch_volume& v = vols[i];
+    ifcm_params pv = *p;
+    pv.c = v.c;
+    ST_TRY(check_shape(v.shape));
+    ST_TRY(check_params(&pv));
+    ST_TRY(check_extent(v.shape, &pv));
+    ST_TRY(check_aligned(v.x, "volume x"));
+    ST_TRY(check_aligned(v.u0, "volume u0"));
+    if (v.P < 1 || v.P > kMaxBatchParticles)
+      return fail(IFCM_ERR_INVALID, "volume %d: P = %d outside 1..%d", i, v.P, kMaxBatchParticles);
+    if (!v.lam_xi || !v.c0 || !v.fitness)
+      return fail(IFCM_ERR_INVALID, "volume %d: lam_xi, c0 and fitness must not be NULL", i);
+  }
+  return IFCM_OK;
+}
+
+// Volumes of cluster count c, in input order.
+std::vector<int> group_of(const ifcm_batch_volume* vols, int n, int c) {
+  std::vector<int> g;
+  for (int i = 0; i < n; ++i)
+    if (vols[i].c == c) g.push_back(i);
+  return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t n,
+                                         const ifcm_params* p) {
+  if (check_multi(vols, n, p) != IFCM_OK) return 0;
+  size_t need = 0;
+  for (int c = 2; c <= kMaxC; ++c) {
+    const std::vector<int> g = group_of(vols, n, c);
+    // whole group, in launch-sized pieces
+    for (size_t b = 0; b < g.size();) {
+      int cnt = 0, parts = 0;
+      while (b + cnt < g.size() && cnt < kMaxVols &&
+             parts + vols[g[b + cnt]].P <= kMaxBatchParticles)
+        parts += vols[g[b + cnt++]].P;
+      const size_t w = wave_bytes(vols, g.data() + b, cnt, c);
+      if (w > need) need = w;
+      b += cnt;
+    }
+  }
+  return need;
+}
+
+size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int32_t n,
+                                             const ifcm_params* p) {
+  if (check_multi(vols, n, p) != IFCM_OK) return 0;
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t w = wave_bytes(vols, &i, 1, vols[i].c);
+    if (w > need) need = w;
+  }
+  return need;
+}
+
+ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
+                              void* ws, size_t ws_bytes, void* stream) {
+  ST_TRY(check_multi(vols, n, p));
+  ST_TRY(check_aligned(ws, "ws"));
+  const size_t min_need = pso_fitness_multi_min_workspace_bytes(vols, n, p);
+  if (ws_bytes < min_need)
+    return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes (the largest volume alone)",
+                ws_bytes, min_need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    // one status word for the whole call: a later wave must not clear an
+    // earlier wave's error
+    Carver cv(ws);
+    CU_TRY(cudaMemsetAsync(carve_status(cv), 0, sizeof(DevStatus), st));
+  }
+  for (int c = 2; c <= kMaxC; ++c) {
+    const std::vector<int> g = group_of(vols, n, c);
+    ifcm_params pc = *p;
+    pc.c = c;
+    for (size_t b = 0; b < g.size();) {
+      // the next wave: as many volumes as fit the launch limits and ws_bytes
+      int cnt = 0, parts = 0;
+      while (b + cnt < g.size() && cnt < kMaxVols &&
+             parts + vols[g[b + cnt]].P <= kMaxBatchParticles &&
+             wave_bytes(vols, g.data() + b, cnt + 1, c) <= ws_bytes)
+        parts += vols[g[b + cnt++]].P;
+      std::vector<BatchVol> bv(cnt);
+      ifcm_shape shapes[kMaxVols];
+      int P[kMaxVols];
+      for (int i = 0; i < cnt; ++i) {
+        const ifcm_batch_volume& v = vols[g[b + i]];
+        bv[i] = BatchVol{v.x, v.shape, v.P, v.lam_xi, v.u0, v.c0, v.fitness, v.iters, nullptr};
+        shapes[i] = v.shape;
+        P[i] = v.P;
+      }
+      Carver cv(ws);
+      DevStatus* status = carve_status(cv);
+      RunBufs rb = carve_runs(cv, shapes, P, cnt, c);
+      CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
+      ST_TRY(run_stencil_batch(bv.data(), cnt, &pc, rb, status, st));
+      b += cnt;
+    }
+  }
+  return IFCM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 // ------------------------------------------------------------- swarm
 static ifcm_status check_swarm(const pso_state* s) {
@@ -699,7 +902,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c.
   ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter, rb,
                    b.iters_init, b.c0, b.J_init, b.status, false, st));
-  CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, b.u0, static_cast<long long>(c) * rpl, st));
+  CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0, static_cast<long long>(c) * rpl, st));
 
   // Algorithm 1 steps 3-9.
   pso_state sw{};
@@ -723,7 +926,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
                      b.c_final, b.status, st));
   if (u_out)
-    CU_TRY(launch_select_copy(rb.ua, rb.ub, rb.st.iters, u_out, static_cast<long long>(c) * rpl,
+    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out, static_cast<long long>(c) * rpl,
                               st));
   CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
                        b.iters_init, b.updates, b.best, b.status, result, st));

@@ -144,17 +144,22 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
   constexpr int NV = 2 * C + 1;
   __shared__ double s_sum[NV][RT];
   __shared__ float s_max[RT];
-  const int p = blockIdx.x;
-  if (!a.st.active[p]) return;
+  const int gp = blockIdx.x;                 // particle of the launch
+  if (!a.st.active[gp]) return;
+  int vi = 0;
+  while (vi + 1 < a.n_vol && a.vol[vi + 1].pbase <= gp) ++vi;
+  const ReduceVol& rv = a.vol[vi];
+  const int p = gp - rv.pbase;               // the volume's particle
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
   float mx = 0.0f;
-  const double* rec = a.partials + static_cast<size_t>(p) * a.n_rec * NV;
-  for (int r = threadIdx.x; r < a.n_rec; r += RT) {
+  const long long first = rv.rec_base + static_cast<long long>(p) * rv.n_rec;
+  const double* rec = a.partials + first * NV;
+  for (int r = threadIdx.x; r < rv.n_rec; r += RT) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] += rec[static_cast<size_t>(r) * NV + v];
-    mx = fmaxf(mx, a.dmax[static_cast<size_t>(p) * a.n_rec + r]);
+    mx = fmaxf(mx, a.dmax[first + r]);
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = acc[v];
@@ -169,22 +174,22 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double* cen = a.st.centres + static_cast<size_t>(p) * C;
+    double* cen = a.st.centres + static_cast<size_t>(gp) * C;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const double S0 = s_sum[j][0], S1 = s_sum[C + j][0];
       if (S0 > 0.0) cen[j] = S1 / S0;                        // Eq 3
-      if (a.c_out) a.c_out[static_cast<size_t>(p) * C + j] = cen[j];
+      if (rv.c_out) rv.c_out[static_cast<size_t>(p) * C + j] = cen[j];
     }
     const double J = s_sum[2 * C][0];                       // Eq 1
-    a.st.J[p] = J;
-    const int it = a.st.iters[p] + 1;
-    a.st.iters[p] = it;
-    if (a.fitness) a.fitness[p] = J;
-    if (a.iters_out) a.iters_out[p] = it;
+    a.st.J[gp] = J;
+    const int it = a.st.iters[gp] + 1;
+    a.st.iters[gp] = it;
+    if (rv.fitness) rv.fitness[p] = J;
+    if (rv.iters_out) rv.iters_out[p] = it;
     const double delta = static_cast<double>(s_max[0]);
-    if (!(delta >= a.eps) || it >= a.max_iter) a.st.active[p] = 0;
-    atomicAdd(a.st.updates, static_cast<unsigned long long>(a.nvox));
+    if (!(delta >= a.eps) || it >= a.max_iter) a.st.active[gp] = 0;
+    atomicAdd(a.st.updates, static_cast<unsigned long long>(rv.nvox));
   }
 }
 
@@ -225,7 +230,7 @@ cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s) 
 }
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s) {
-  PIFCM_DISPATCH_C(c, (reduce_kernel<C><<<a.P, RT, 0, s>>>(a)); return cudaGetLastError());
+  PIFCM_DISPATCH_C(c, (reduce_kernel<C><<<a.P_total, RT, 0, s>>>(a)); return cudaGetLastError());
 }
 
 cudaError_t launch_run_init(int c, int P, const double* c0, RunState st, double* J_clear,

@@ -102,31 +102,45 @@ __device__ __forceinline__ float gdist(float a, float b) {
 }
 
 struct Item {
-  int p0, p1;          // particles of the group (p1 = p0 when the group has one)
+  int v;               // volume
+  int p0, p1;          // the volume's particles of the group (p1 = p0 when the group has one)
   bool two;            // p1 is a distinct particle
   int tile, x0, y0, z0, z1, pzb, pze;
 };
 
+// Work items of a launch, numbered volume by volume: the active particles of
+// volume v (s_act[vfirst[v] ...], vnact[v] of them) in groups of NP, times the
+// volume's tiles; vitem[v] is the volume's first item.
+struct ItemTable {
+  short act[kMaxBatchParticles];
+  int vfirst[kMaxVols], vnact[kMaxVols], vitem[kMaxVols + 1];
+};
+
 template <int NP>
-__device__ __forceinline__ Item decode_item(const StencilArgs& a, const int* act, int nact,
-                                            int w) {
+__device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTable& tab, int w) {
   Item it;
-  const int g = w / a.n_tiles;
-  it.tile = w - g * a.n_tiles;
+  int v = 0;
+  while (v + 1 < a.n_vol && tab.vitem[v + 1] <= w) ++v;
+  const VolDesc& vd = a.vol[v];
+  it.v = v;
+  const int wl = w - tab.vitem[v];
+  const int g = wl / vd.n_tiles;
+  it.tile = wl - g * vd.n_tiles;
+  const short* act = tab.act + tab.vfirst[v];
   it.p0 = act[g * NP];
-  it.two = (NP == 2) && (g * NP + 1 < nact);
+  it.two = (NP == 2) && (g * NP + 1 < tab.vnact[v]);
   it.p1 = it.two ? act[g * NP + 1] : it.p0;
-  const int per_z = a.tiles_x * a.tiles_y;
+  const int per_z = vd.tiles_x * vd.tiles_y;
   const int zc = it.tile / per_z;
   const int rem = it.tile - zc * per_z;
-  const int ty = rem / a.tiles_x;
-  const int tx = rem - ty * a.tiles_x;
+  const int ty = rem / vd.tiles_x;
+  const int tx = rem - ty * vd.tiles_x;
   it.x0 = tx * TX;
   it.y0 = ty * TY;
-  it.z0 = zc * a.tz;
-  it.z1 = min(it.z0 + a.tz, a.nz);
+  it.z0 = zc * vd.tz;
+  it.z1 = min(it.z0 + vd.tz, vd.nz);
   it.pzb = max(it.z0 - 1, 0);
-  it.pze = min(it.z1, a.nz - 1);
+  it.pze = min(it.z1, vd.nz - 1);
   return it;
 }
 
@@ -272,7 +286,7 @@ __device__ __forceinline__ float2 max2(float2 v, float lo) {
 template <int C, int NP>
 __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
                                                 int cidx, float xc, int z, bool interior,
-                                                const StencilArgs& a, const Item& it,
+                                                const VolDesc& a, const Item& it,
                                                 const ItemConst<C, NP>& ic, const Ctx& cx,
                                                 const MethodConsts& k, Sums<C, NP>& acc) {
   constexpr int K = Pairs<C, NP>::K;
@@ -415,13 +429,11 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
 
 template <int C, int NP>
 __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
-    stencil_kernel(const __grid_constant__ CUtensorMap tm_x,
-                   const __grid_constant__ CUtensorMap tm_u, const StencilArgs a) {
+    stencil_kernel(const __grid_constant__ StencilArgs a) {
   extern __shared__ unsigned char dsmem_raw[];
   __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ __align__(8) uint64_t empty[NSTAGE];
-  __shared__ int s_act[kMaxP];
-  __shared__ int s_nact;
+  __shared__ ItemTable tab;
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
   __shared__ ItemConst<C, NP> s_ic;
@@ -431,11 +443,23 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  if (tid == 0) {
+  // Active particles of every volume, compacted one volume per warp (ballots).
+  for (int v = warp; v < a.n_vol; v += NT / 32) {
+    const VolDesc& vd = a.vol[v];
     int n = 0;
-    for (int p = 0; p < a.P; ++p)
-      if (a.active[p]) s_act[n++] = p;
-    s_nact = n;
+    for (int base = 0; base < vd.P; base += 32) {
+      const int p = base + lane;
+      const bool on = p < vd.P && a.active[vd.pbase + p] != 0;
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) tab.act[vd.pbase + n + __popc(m & ((1u << lane) - 1u))] = static_cast<short>(p);
+      n += __popc(m);
+    }
+    if (lane == 0) {
+      tab.vfirst[v] = vd.pbase;
+      tab.vnact[v] = n;
+    }
+  }
+  if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
@@ -444,9 +468,16 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     fence_mbarrier_init();
   }
   __syncthreads();
-  const int nact = s_nact;
-  const int groups = (nact + NP - 1) / NP;
-  const int n_items = groups * a.n_tiles;
+  if (tid == 0) {
+    int items = 0;
+    for (int v = 0; v < a.n_vol; ++v) {
+      tab.vitem[v] = items;
+      items += ((tab.vnact[v] + NP - 1) / NP) * a.vol[v].n_tiles;
+    }
+    tab.vitem[a.n_vol] = items;
+  }
+  __syncthreads();
+  const int n_items = tab.vitem[a.n_vol];
   if (static_cast<int>(blockIdx.x) >= n_items) return;
 
   auto xs_of = [&](int s) { return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP>()); };
@@ -457,11 +488,12 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   // ------------------------------------------------------------ producer
   if (warp == NCW) {
     if (lane == 0) {
-      prefetch_tensormap(&tm_x);
-      prefetch_tensormap(&tm_u);
       int q = 0;
       for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const Item it = decode_item<NP>(a, s_act, nact, w);
+        const Item it = decode_item<NP>(a, tab, w);
+        const VolDesc& vd = a.vol[it.v];
+        const CUtensorMap* mx = &a.tm_x[it.v];
+        const CUtensorMap* mu = &a.tm_u[it.v];
         for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
           const int s = q % NSTAGE;
           if (q >= NSTAGE &&
@@ -472,12 +504,12 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
           }
           if (*reinterpret_cast<volatile int*>(&s_abort)) return;
           mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP>());
-          tma_load_3d(xs_of(s), &tm_x, &full[s], it.x0 - 4, it.y0 - 1, pz);
-          tma_load_4d(us_of(s), &tm_u, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                      it.p0 * a.src_cstride);
+          tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
+          tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
+                      it.p0 * vd.src_cstride);
           if (NP == 2)
-            tma_load_4d(us_of(s) + ufloats<C>(), &tm_u, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                        it.p1 * a.src_cstride);
+            tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
+                        it.p1 * vd.src_cstride);
         }
       }
     }
@@ -492,8 +524,6 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   k.m = a.m;
   k.inv_m1 = a.inv_m1;
   k.m_is_2 = a.m_is_2;
-  const bool z3 = a.nz > 1;
-  const int plane = a.nz * a.ny * a.pitch;
   int q = 0;
 
   // Waits for plane qq's stage (bounded; after a timeout every wait is skipped
@@ -513,51 +543,51 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   };
 
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const Item it = decode_item<NP>(a, s_act, nact, w);
+    const Item it = decode_item<NP>(a, tab, w);
+    const VolDesc& vd = a.vol[it.v];
+    const bool z3 = vd.nz > 1;
+    const int plane = vd.nz * vd.ny * vd.pitch;
     Ctx cx;
     cx.X = it.x0 + tx;
     cx.Y = it.y0 + ty;
-    cx.col_ok = (cx.X < a.nx) && (cx.Y < a.ny);
-    cx.col_interior = cx.X > 0 && cx.X < a.nx - 1 && cx.Y > 0 && cx.Y < a.ny - 1;
-    cx.col_off = cx.Y * a.pitch + cx.X;
+    cx.col_ok = (cx.X < vd.nx) && (cx.Y < vd.ny);
+    cx.col_interior = cx.X > 0 && cx.X < vd.nx - 1 && cx.Y > 0 && cx.Y < vd.ny - 1;
+    cx.col_off = cx.Y * vd.pitch + cx.X;
     if (tid == 0) {
       float lam[2], xi[2], cc[2][C];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int pid = (p == 0 || NP == 1) ? it.p0 : it.p1;
-        lam[p] = static_cast<float>(a.lam_xi[2 * pid]);
-        xi[p] = static_cast<float>(a.lam_xi[2 * pid + 1]);
+        lam[p] = static_cast<float>(vd.lam_xi[2 * pid]);
+        xi[p] = static_cast<float>(vd.lam_xi[2 * pid + 1]);
 #pragma unroll
-        for (int j = 0; j < C; ++j) cc[p][j] = static_cast<float>(a.centres[pid * C + j]);
-        if (p < NP) s_ic.dst[p] = a.u_dst + static_cast<size_t>(pid) * C * plane;
+        for (int j = 0; j < C; ++j)
+          cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
+        if (p < NP) s_ic.dst[p] = vd.u_dst + static_cast<size_t>(pid) * C * plane;
       }
       s_ic.nlam = make_float2(-lam[0], -lam[1]);
       s_ic.nxi = make_float2(-xi[0], -xi[1]);
 #pragma unroll
-      for (int q = 0; q < Pairs<C, NP>::K; ++q) {
-        if (NP == 2) s_ic.ncc[q] = make_float2(-cc[0][q], -cc[1][q]);
-        else s_ic.ncc[q] = make_float2(-cc[0][2 * q], 2 * q + 1 < C ? -cc[0][2 * q + 1] : 0.0f);
+      for (int qk = 0; qk < Pairs<C, NP>::K; ++qk) {
+        if (NP == 2) s_ic.ncc[qk] = make_float2(-cc[0][qk], -cc[1][qk]);
+        else s_ic.ncc[qk] = make_float2(-cc[0][2 * qk], 2 * qk + 1 < C ? -cc[0][2 * qk + 1] : 0.0f);
       }
     }
     consumer_sync();
-    Slot<C, NP> s0, s1, s2;
-    s0.clear();
-    s1.clear();
-    s2.clear();
+    Slot<C, NP> sd, sl, sm, sh;
+    sd.clear();
+    sl.clear();
+    sm.clear();
+    sh.clear();
     Sums<C, NP> acc;
     acc.clear();
     const int np = it.pze - it.pzb + 1;
     const int q0 = q;
 
-    // Delayed finalisation: the centre completed by plane pz - 1 is finalised
-    // while plane pz accumulates, in one basic block, so that the long
-    // dependency chain of Eqs 4 and 2 overlaps the stencil arithmetic.
-    // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1.
-    Slot<C, NP>& sd = s0;
-    Slot<C, NP>& sl = s1;
-    Slot<C, NP>& sm = s2;
-    Slot<C, NP> sh;
-    sh.clear();
+    // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1 while
+    // plane pz is consumed.  The centre completed by plane pz - 1 is finalised
+    // in the same basic block as plane pz's stencil so that its dependency
+    // chain (Eqs 4 and 2) overlaps the stencil arithmetic.
     for (int kk = 0; kk < np; ++kk) {
       const int qq = q0 + kk;
       const int pz = it.pzb + kk;
@@ -573,8 +603,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
           const int sdi = (qq + NSTAGE - 2) % NSTAGE;
           finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
-                                 cx.col_interior && zd > 0 && zd < a.nz - 1, a, it, s_ic, cx, k,
-                                 acc);
+                                 cx.col_interior && zd > 0 && zd < vd.nz - 1, vd, it, s_ic, cx,
+                                 k, acc);
         }
         if (z3)
           accumulate_plane<C, NP, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
@@ -595,13 +625,13 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
         const int sdi = (ql + NSTAGE - 1) % NSTAGE;
         finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
-                               cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < a.nz - 1, a,
+                               cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
                                it, s_ic, cx, k, acc);
       }
-      if (live && it.pze == a.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
+      if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
         const int sli = ql % NSTAGE;
         finalize_centre<C, NP>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
-                               cx.col_interior && !z3, a, it, s_ic, cx, k, acc);
+                               cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
       }
       if (np >= 2) release(ql - 1);
       release(ql);
@@ -632,7 +662,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       const int p = tid / (2 * C + 2), v = tid - p * (2 * C + 2);
       if (p == 0 || it.two) {
         const int pid = p == 0 ? it.p0 : it.p1;
-        const size_t rec = static_cast<size_t>(pid) * a.n_tiles + it.tile;
+        const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
         if (v < 2 * C + 1) {
           double sum = 0.0;
 #pragma unroll
@@ -649,16 +679,14 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     consumer_sync();
   }
 }
-
 // ---------------------------------------------------------------------------
 template <int C, int NP>
-cudaError_t launch_c(const CUtensorMap& tm_x, const CUtensorMap& tm_u, const StencilArgs& a,
-                     int grid, cudaStream_t s) {
+cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
   constexpr int smem = smem_total<C, NP>();
   cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil_kernel<C, NP><<<grid, NT, smem, s>>>(tm_x, tm_u, a);
+  stencil_kernel<C, NP><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -708,16 +736,15 @@ int stencil_blocks_per_sm(int c) {
   }
 }
 
-cudaError_t launch_stencil(int c, const CUtensorMap& tm_x, const CUtensorMap& tm_u,
-                           const StencilArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_stencil(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, np_for<2>()>(tm_x, tm_u, a, grid, s);
-    case 3: return launch_c<3, np_for<3>()>(tm_x, tm_u, a, grid, s);
-    case 4: return launch_c<4, np_for<4>()>(tm_x, tm_u, a, grid, s);
-    case 5: return launch_c<5, np_for<5>()>(tm_x, tm_u, a, grid, s);
-    case 6: return launch_c<6, np_for<6>()>(tm_x, tm_u, a, grid, s);
-    case 7: return launch_c<7, np_for<7>()>(tm_x, tm_u, a, grid, s);
-    case 8: return launch_c<8, np_for<8>()>(tm_x, tm_u, a, grid, s);
+    case 2: return launch_c<2, np_for<2>()>(a, grid, s);
+    case 3: return launch_c<3, np_for<3>()>(a, grid, s);
+    case 4: return launch_c<4, np_for<4>()>(a, grid, s);
+    case 5: return launch_c<5, np_for<5>()>(a, grid, s);
+    case 6: return launch_c<6, np_for<6>()>(a, grid, s);
+    case 7: return launch_c<7, np_for<7>()>(a, grid, s);
+    case 8: return launch_c<8, np_for<8>()>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

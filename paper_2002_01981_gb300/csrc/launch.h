@@ -16,30 +16,46 @@ constexpr int kTX = 32;
 constexpr int kTY = 8;
 constexpr int kThreads = kTX * kTY;
 
-struct StencilArgs {
+// One volume of a stencil launch.  A launch covers up to kMaxVols volumes of
+// the same c; particle state arrays (centres, active) are shared by the
+// launch and indexed by the volume's first particle pbase.
+constexpr int kMaxVols = 64;
+constexpr int kMaxBatchParticles = 4096;
+
+struct VolDesc {
   int nx, ny, nz, pitch;
-  int tiles_x, tiles_y, zchunks, tz;
-  int n_tiles;                  // tiles_x * tiles_y * zchunks, per particle
-  int P;                        // particles in the batch
+  int tiles_x, tiles_y, tz, n_tiles;   // 32x8 column tiles x z-chunks of tz planes
+  int P;                        // particles of this volume in the batch
+  int pbase;                    // index of its particle 0 in the launch's state arrays
+  long long rec_base;           // first partial record: record = rec_base + p * n_tiles + tile
   const double* lam_xi;         // [P][2]
-  const double* centres;        // [P][c]  C^t
-  const int32_t* active;        // [P]
   float* u_dst;                 // [P][c][nz][ny][pitch]  U^{t+1}
   const float* u_src;           // particle 0's U^t (for the rare flat-neighbourhood path)
   long long src_pstride;        // elements between particles' U^t (0: one shared U^t)
   int src_cstride;              // TMA cluster-coordinate step per particle (c or 0)
-  double* partials;             // [P][n_tiles][2c+1]
-  float* dmax;                  // [P][n_tiles]
+};
+
+// Kernel parameter block (passed as __grid_constant__, so the tensor maps
+// stay in parameter space): the volumes, their TMA maps, the shared state.
+struct StencilArgs {
+  CUtensorMap tm_x[kMaxVols];   // normalised volume (NaN outside)
+  CUtensorMap tm_u[kMaxVols];   // memberships U^t (zero outside)
+  VolDesc vol[kMaxVols];
+  int n_vol;
+  const double* centres;        // [particles of the launch][c]  C^t
+  const int32_t* active;        // [particles of the launch]
+  double* partials;             // [records][2c+1]
+  float* dmax;                  // [records]
   float dist_floor, m, inv_m1;
   int m_is_2;
   DevStatus* status;
 };
+static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
 
 int stencil_particles_per_item(int c);   // particles sharing one work item
 size_t stencil_smem_bytes(int c);
 int stencil_blocks_per_sm(int c);
-cudaError_t launch_stencil(int c, const CUtensorMap& tm_x, const CUtensorMap& tm_u,
-                           const StencilArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_stencil(int c, const StencilArgs& a, int grid, cudaStream_t s);
 
 // ------------------------------------- plain iteration (one thread per voxel)
 struct PlainArgs {
@@ -64,18 +80,27 @@ int plain_blocks(long long nvox, int vpt);
 cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s);
 
 // ---------------------------------------------- per-particle finalisation
-struct ReduceArgs {
-  int P, n_rec;                 // particles; partial records per particle
-  const double* partials;       // [P][n_rec][2c+1]
-  const float* dmax;            // [P][n_rec]
-  RunState st;
+// One volume of a reduce launch (particle p of the volume is state index
+// pbase + p; its records are rec_base + p * n_rec ... + n_rec - 1).
+struct ReduceVol {
+  int pbase, P, n_rec;
+  long long rec_base;
+  long long nvox;
   double* fitness;              // [P] or NULL
   int32_t* iters_out;           // [P] or NULL
   double* c_out;                // [P][c] or NULL
+};
+
+struct ReduceArgs {
+  int n_vol;
+  int P_total;                  // particles of the launch (one CTA each)
+  const double* partials;       // [records][2c+1]
+  const float* dmax;            // [records]
+  RunState st;                  // arrays over the launch's particles
   int max_iter;
   double eps;
-  long long nvox;
   DevStatus* status;
+  ReduceVol vol[kMaxVols];
 };
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s);

@@ -165,6 +165,65 @@ def pso_fitness_batch(x, params, lam_xi, u0, c0, nx=None, ws=None, want_centres=
     return fit, its, cout
 
 
+# ------------------------------- Alg 1 step 4, many swarms on many volumes
+@dataclass
+class BatchVolume:
+    """One volume of ``pso_fitness_multi``: its normalised volume, cluster
+    count, particles (lam_xi [P, 2]) and the shared start (u0, c0)."""
+    x: torch.Tensor
+    c: int
+    lam_xi: object
+    u0: torch.Tensor
+    c0: object
+    nx: int = None
+
+
+def _multi_descriptors(volumes):
+    descs = (N.IfcmBatchVolume * len(volumes))()
+    keep, outs = [], []
+    for i, v in enumerate(volumes):
+        _check_cuda(v.x, torch.float32, f"volumes[{i}].x")
+        _check_cuda(v.u0, torch.float32, f"volumes[{i}].u0")
+        dev = v.x.device
+        lx = _lam_xi_tensor(v.lam_xi, dev).reshape(-1, 2).contiguous()
+        c0 = _lam_xi_tensor(v.c0, dev)
+        P = lx.shape[0]
+        fit = torch.empty(P, dtype=torch.float64, device=dev)
+        its = torch.empty(P, dtype=torch.int32, device=dev)
+        keep += [lx, c0]
+        outs.append((fit, its))
+        descs[i] = N.IfcmBatchVolume(v.x.data_ptr(), shape_of(v.x, v.nx), int(v.c), int(P),
+                                     lx.data_ptr(), v.u0.data_ptr(), c0.data_ptr(),
+                                     fit.data_ptr(), its.data_ptr())
+    return descs, keep, outs
+
+
+def pso_fitness_multi_workspace_bytes(volumes, params, minimum=False):
+    lib = N.load()
+    descs, _keep, _ = _multi_descriptors(volumes)
+    p = params.native()
+    fn = (lib.pso_fitness_multi_min_workspace_bytes if minimum
+          else lib.pso_fitness_multi_workspace_bytes)
+    return fn(descs, len(volumes), ctypes.byref(p))
+
+
+def pso_fitness_multi(volumes, params, ws=None):
+    """Fitness of every particle of every volume (volumes of the same c share
+    each batched launch); ``params.c`` is ignored, each volume has its own.
+    Returns a list of (fitness [P] float64, iterations [P] int32)."""
+    lib = N.load()
+    descs, _keep, outs = _multi_descriptors(volumes)
+    p = params.native()
+    dev = volumes[0].x.device
+    if ws is None:
+        ws = workspace(lib.pso_fitness_multi_workspace_bytes(descs, len(volumes),
+                                                             ctypes.byref(p)), dev)
+    N.check(lib.pso_fitness_multi(descs, len(volumes), ctypes.byref(p), _ptr(ws), ws.numel(),
+                                  _stream()))
+    N.check(device_status(ws))
+    return outs
+
+
 # ------------------------------------------------------ Alg 1 steps 3, 5-8
 class Swarm:
     """Device-resident swarm; ``init`` is step 3, ``step`` steps 5-8."""

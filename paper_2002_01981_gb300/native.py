@@ -45,6 +45,12 @@ class PifcmResult(Structure):
                 ("best_particle", c_int32)]
 
 
+class IfcmBatchVolume(Structure):
+    _fields_ = [("x", c_void_p), ("shape", IfcmShape), ("c", c_int32), ("P", c_int32),
+                ("lam_xi", c_void_p), ("u0", c_void_p), ("c0", c_void_p),
+                ("fitness", c_void_p), ("iters", c_void_p)]
+
+
 # name -> (restype, argtypes); the exported symbols of include/pifcm.h
 SIGNATURES = {
     "ifcm_status_string": (c_char_p, [c_int32]),
@@ -62,6 +68,12 @@ SIGNATURES = {
     "pso_fitness_batch_workspace_bytes": (c_size_t, [IfcmShape, POINTER(IfcmParams), c_int32]),
     "pso_fitness_batch": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), c_void_p,
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_size_t, c_void_p]),
+    "pso_fitness_multi_workspace_bytes": (c_size_t, [POINTER(IfcmBatchVolume), c_int32,
+                                                     POINTER(IfcmParams)]),
+    "pso_fitness_multi_min_workspace_bytes": (c_size_t, [POINTER(IfcmBatchVolume), c_int32,
+                                                         POINTER(IfcmParams)]),
+    "pso_fitness_multi": (c_int32, [POINTER(IfcmBatchVolume), c_int32, POINTER(IfcmParams),
                                     c_void_p, c_size_t, c_void_p]),
     "pso_init": (c_int32, [POINTER(PsoState), c_void_p]),
     "pso_step": (c_int32, [POINTER(PsoState), c_void_p, c_void_p]),

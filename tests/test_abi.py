@@ -146,3 +146,54 @@ def test_options_validation(lib):
 def test_status_strings(lib):
     for s in range(7):
         assert lib.ifcm_status_string(s)
+
+
+def _batch_volumes(specs):
+    """Descriptors with fake (aligned, never dereferenced) device pointers."""
+    from paper_2002_01981_gb300 import native as N
+    arr = (N.IfcmBatchVolume * len(specs))()
+    for i, (shape, c, P) in enumerate(specs):
+        arr[i] = N.IfcmBatchVolume(256, N.IfcmShape(*shape), c, P, 256, 256, 256, 256, 0)
+    return arr
+
+
+def test_multi_volume_layout_and_validation(lib):
+    from paper_2002_01981_gb300 import native as N
+    assert ctypes.sizeof(N.IfcmBatchVolume) == 8 + 16 + 4 + 4 + 5 * 8
+    p = _params()
+    fake = ctypes.c_void_p(256)
+    ok = _batch_volumes([((20, 16, 12, 20), 3, 4)])
+    assert lib.pso_fitness_multi(ok, 0, ctypes.byref(p), fake, 1 << 40, None) == 1
+    for bad in ([((20, 16, 12, 20), 9, 4)], [((20, 16, 12, 20), 3, 0)],
+                [((20, 16, 12, 18), 3, 4)], [((20, 16, 12, 20), 3, 5000)]):
+        assert lib.pso_fitness_multi(_batch_volumes(bad), 1, ctypes.byref(p), fake, 1 << 40,
+                                     None) == 1
+        assert lib.pso_fitness_multi_workspace_bytes(_batch_volumes(bad), 1, ctypes.byref(p)) == 0
+    # a workspace below what the largest volume needs alone is refused before any launch
+    need = lib.pso_fitness_multi_min_workspace_bytes(ok, 1, ctypes.byref(p))
+    assert need > 0
+    assert lib.pso_fitness_multi(ok, 1, ctypes.byref(p), fake, need - 256, None) == 2
+
+
+def test_multi_volume_workspace_is_the_largest_wave(lib):
+    from paper_2002_01981_gb300 import native as N
+    p = _params()
+    a = ((40, 32, 24, 40), 3, 6)
+    b = ((24, 24, 24, 24), 3, 5)
+    d = ((64, 48, 40, 64), 5, 2)
+    one = lambda s: lib.pso_fitness_multi_workspace_bytes(_batch_volumes([s]), 1, ctypes.byref(p))
+    both = lib.pso_fitness_multi_workspace_bytes(_batch_volumes([a, b]), 2, ctypes.byref(p))
+    # volumes of one c share a wave: their buffers add up
+    assert both >= one(a) + one(b) - (1 << 16)
+    mixed = _batch_volumes([a, d, b])
+    # groups of different c run one after the other in the same workspace
+    full = lib.pso_fitness_multi_workspace_bytes(mixed, 3, ctypes.byref(p))
+    assert full == max(both, one(d))
+    lo = lib.pso_fitness_multi_min_workspace_bytes(mixed, 3, ctypes.byref(p))
+    assert lo == max(one(a), one(b), one(d))
+    # one volume needs what the single-volume batch entry needs, give or take
+    # the alignment slack
+    shp = N.IfcmShape(*a[0])
+    pc = _params(c=3)
+    single = lib.pso_fitness_batch_workspace_bytes(shp, ctypes.byref(pc), 6)
+    assert abs(one(a) - single) <= 4096

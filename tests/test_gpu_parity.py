@@ -329,3 +329,76 @@ def test_pifcm3d_slice_mode(G):
     U0, C0, _, _ = O.fcm_init(x, 3, 2.0, 30, 0.0)
     bound = u_bound(x, U0, C0, ref["lambda"], ref["xi"], 5)
     assert np.max(np.abs(unpad(U, 22) - ref["U"])) <= bound
+
+
+# ------------------------------------------- many volumes in one launch
+MULTI_SPECS = [((9, 14, 21), 3, 3), ((16, 12, 33), 4, 5), ((5, 30, 17), 3, 1),
+               ((12, 12, 12), 6, 4), ((20, 9, 40), 4, 2), ((1, 40, 37), 4, 3)]
+
+
+def _multi_inputs(G, specs, seed):
+    vols, host = [], []
+    for k, (shape, c, P) in enumerate(specs):
+        x = unit_volume(shape, seed=seed + k)
+        U0 = phantoms.random_memberships(shape, c, seed=seed + 100 + k)
+        C0 = np.sort(np.random.default_rng(seed + 200 + k).random(c))
+        lam_xi = np.random.default_rng(seed + 300 + k).random((P, 2))
+        vols.append(G.BatchVolume(dev_vol(x), c, lam_xi, dev_u(U0), C0, nx=shape[2]))
+        host.append((x, U0, C0, lam_xi))
+    return vols, host
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-5])
+def test_fitness_multi_equals_single_volume_runs(G, eps):
+    vols, _ = _multi_inputs(G, MULTI_SPECS, seed=61)
+    prm = G.Params(max_iter=12, eps_u=eps)
+    outs = G.pso_fitness_multi(vols, prm)
+    for v, (fit, its) in zip(vols, outs):
+        pc = G.Params(c=v.c, max_iter=12, eps_u=eps)
+        f1, i1, _ = G.pso_fitness_batch(v.x, pc, v.lam_xi, v.u0, v.c0, nx=v.nx)
+        # same arithmetic per (particle, tile) and a fixed reduction order
+        assert torch.equal(fit, f1)
+        assert torch.equal(its, i1)
+
+
+def test_fitness_multi_matches_oracle(G):
+    vols, host = _multi_inputs(G, MULTI_SPECS, seed=71)
+    outs = G.pso_fitness_multi(vols, G.Params(max_iter=8, eps_u=0.0))
+    for (x, U0, C0, lam_xi), (fit, its) in zip(host, outs):
+        fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
+                                  max_iter=8, eps=0.0)
+        assert np.array_equal(its.cpu().numpy(), io)
+        assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
+
+
+def test_fitness_multi_in_workspace_sized_waves(G):
+    # the smallest workspace runs one volume per wave; results do not change
+    vols, _ = _multi_inputs(G, MULTI_SPECS, seed=81)
+    prm = G.Params(max_iter=6, eps_u=1e-5)
+    full = G.pso_fitness_multi(vols, prm)
+    lo = G.pso_fitness_multi_workspace_bytes(vols, prm, minimum=True)
+    assert lo < G.pso_fitness_multi_workspace_bytes(vols, prm)
+    small = G.pso_fitness_multi(vols, prm, ws=G.workspace(lo))
+    for (fa, ia), (fb, ib) in zip(full, small):
+        assert torch.equal(fa, fb) and torch.equal(ia, ib)
+
+
+def test_fitness_multi_beyond_one_launch(G):
+    # 70 volumes (more than one launch holds) and 5000 particles on 5 volumes
+    # (more particles than one launch holds) split into several launches
+    specs = [((3 + k % 5, 4 + k % 3, 5 + k % 7), 2 + k % 3, 1 + k % 2) for k in range(70)]
+    vols, _ = _multi_inputs(G, specs, seed=91)
+    prm = G.Params(max_iter=4, eps_u=0.0)
+    outs = G.pso_fitness_multi(vols, prm)
+    for v, (fit, its) in zip(vols, outs):
+        f1, i1, _ = G.pso_fitness_batch(v.x, G.Params(c=v.c, max_iter=4, eps_u=0.0), v.lam_xi,
+                                        v.u0, v.c0, nx=v.nx)
+        assert torch.equal(fit, f1) and torch.equal(its, i1)
+    big = [((4, 6, 8), 3, 1000), ((5, 5, 9), 3, 1000), ((6, 4, 7), 3, 1000),
+           ((3, 7, 8), 3, 1000), ((4, 4, 4), 3, 1000)]
+    vols, _ = _multi_inputs(G, big, seed=95)
+    outs = G.pso_fitness_multi(vols, prm)
+    for v, (fit, its) in zip(vols, outs):
+        f1, i1, _ = G.pso_fitness_batch(v.x, G.Params(c=3, max_iter=4, eps_u=0.0), v.lam_xi,
+                                        v.u0, v.c0, nx=v.nx)
+        assert torch.equal(fit, f1) and torch.equal(its, i1)
