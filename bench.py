@@ -41,7 +41,6 @@ WORKLOAD = ("brain stand-in 181x217x181 (nested ellipsoids 0/0.25/0.55/0.85, +-1
             "Rician sigma 0.07), c=4, m=2, 26-neighbourhood, 20 particles x 30 generations, "
             "<=50 IFCM iterations per fitness, stop max|du|<1e-5")
 CPU_SLAB = 48                      # z-planes of the oracle's bounded sample
-PARTICLES_PER_ITEM = 2             # particles sharing one stencil work item at c = 4
 
 
 def peaks():
@@ -136,7 +135,8 @@ def rank_seed(rank):
 
 def stencil_source_sha():
     h = hashlib.sha256()
-    for name in ("ifcm_stencil.cu", "ifcm_math.cuh", "common.cuh", "launch.h"):
+    for name in ("stencil_kernel.cuh", "ifcm_stencil.cu", "ifcm_stencil_np2.cu", "ifcm_math.cuh",
+                 "common.cuh", "launch.h", "api.cu"):
         with open(os.path.join(ROOT, "paper_2002_01981_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -343,7 +343,8 @@ def run_ours(args):
     # ---- roofline of the stencil kernel (dominant kernel)
     hbm, peak_kind = peaks()
     # U^t read + U^{t+1} write + x read once per item, shared by the item's particles
-    bytes_per_update = 2 * C * 4 + 4.0 / PARTICLES_PER_ITEM
+    plan_np, plan_tz, _ = G.stencil_plan(G.shape_of(vol, nx), C, P)
+    bytes_per_update = 2 * C * 4 + 4.0 / plan_np
     per_launch_updates = stencil_updates_step * args.steps / max(kernel_launches, 1)
     achieved = (stencil_updates_step * args.steps * bytes_per_update) / (kernel_ms / 1e3) / 1e9
     traffic_pu = stencil_traffic_per_update()
@@ -351,7 +352,10 @@ def run_ours(args):
                 "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic_pu * per_launch_updates if traffic_pu else None,
                 "algorithmic_bytes_per_launch": per_launch_updates * bytes_per_update,
-                "kernel": "stencil_kernel<4>", "kernel_ms_total": kernel_ms,
+                "kernel": f"stencil_kernel<4,{plan_np}>",
+                "plan": {"particles_per_item": plan_np, "tz": plan_tz,
+                         "tile": "32x11 columns"},
+                "kernel_ms_total": kernel_ms,
                 "kernel_launches": kernel_launches,
                 "kernel_share_of_step": kernel_ms / ms}
 

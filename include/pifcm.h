@@ -175,6 +175,28 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
                               void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Work decomposition of the batched stencil launches (no arithmetic change
+ * beyond the order of the FP64 partial sums).  A launch is cut into work
+ * items of np particles (1, or 2 for c <= 4) x a 32-column tile x a z-chunk
+ * of tz planes.  Mode 0 (default): a built-in rule picks the deepest chunks
+ * that still give every CTA four items.  Mode 1: the first run of each
+ * (membership type, c, volume extents, particle counts) times the candidate
+ * plans on its own buffers (a host synchronisation; never on a stream being
+ * captured into a graph) and the fastest is cached for the process.
+ * Thread-safe.
+ */
+void ifcm_autotune_enable(int32_t mode);
+void ifcm_autotune_reset(void);
+/* Every later launch uses np particles per item (where c allows it: np = 2
+ * only for c <= 4, else the usual choice) and `chunks` z-chunks per tile
+ * (clamped so that chunks keep >= 8 planes).  np = 0 lifts it.  For tests
+ * and experiments.  IFCM_ERR_INVALID for np outside 0..2 or chunks < 1. */
+ifcm_status ifcm_stencil_force_plan(int32_t np, int32_t chunks);
+/* The plan a one-volume batch of P particles would use: *np, *tz.  Returns 1
+ * when it comes from the tuning cache, 0 from the rule, -1 on bad input. */
+int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, int32_t* tz);
+
+/* ---------------------------------------------------------------------------
  * Algorithm 1 step 4 for many swarms at once: each volume brings its own
  * particles, start (u0, c0) and cluster count, and every (volume, particle)
  * fitness is evaluated in the same batched launches: volumes of the same c
@@ -205,6 +227,19 @@ size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int3
                                              const ifcm_params* p);
 ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
                               void* ws, size_t ws_bytes, void* stream);
+
+/* The same call captured once into a CUDA graph: every replay re-runs it with
+ * the values then in the buffers (the swarm's new lam_xi each generation)
+ * and the same pointers, which must stay valid while the graph lives.  The
+ * plan of each launch is fixed at capture (the cache, else the rule; no
+ * timing).  Replays on one workspace must not overlap.  Checks as for
+ * pso_fitness_multi; IFCM_ERR_CUDA when capture or instantiation fails. */
+typedef struct ifcm_graph_t* ifcm_graph;
+ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
+                                    const ifcm_params* p, void* ws, size_t ws_bytes,
+                                    ifcm_graph* out);
+ifcm_status ifcm_graph_launch(ifcm_graph g, void* stream);
+void ifcm_graph_destroy(ifcm_graph g);
 
 /* ---------------------------------------------------------------------------
  * Algorithm 1 step 3: x ~ U[0,1)^2, v ~ U[-vmax, vmax)^2, pbest_x = x,

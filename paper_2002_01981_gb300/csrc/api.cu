@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -105,15 +106,26 @@ struct Tiling {
   int tiles_x, tiles_y, zchunks, tz, n_tiles;
 };
 
-Tiling tiling(const ifcm_shape& s) {
+// A work item covers ceil(nz / chunks) planes of one 32 x kTY column tile.
+// Chunks never get shorter than kMinTileZ planes (unless the volume is), so
+// a particle never has more than max_chunks(nz) x tiles_xy records.
+constexpr int kMinTileZ = 8;
+
+int max_chunks(int nz) { return nz <= kMinTileZ ? 1 : (nz + kMinTileZ - 1) / kMinTileZ; }
+
+Tiling tiling(const ifcm_shape& s, int chunks) {
   Tiling t;
   t.tiles_x = (s.nx + kTX - 1) / kTX;
   t.tiles_y = (s.ny + kTY - 1) / kTY;
-  t.tz = s.nz < 32 ? s.nz : 32;
+  const int k = chunks < 1 ? 1 : (chunks > max_chunks(s.nz) ? max_chunks(s.nz) : chunks);
+  t.tz = (s.nz + k - 1) / k;
   t.zchunks = (s.nz + t.tz - 1) / t.tz;
   t.n_tiles = t.tiles_x * t.tiles_y * t.zchunks;
   return t;
 }
+
+// Most records one particle of this volume can have (any plan).
+int max_tiles(const ifcm_shape& s) { return tiling(s, max_chunks(s.nz)).n_tiles; }
 
 constexpr int kPlainVpt = 32;
 
@@ -143,7 +155,7 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
     r.ua[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
     r.ub[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
     const long long nvox = static_cast<long long>(shapes[v].nx) * shapes[v].ny * shapes[v].nz;
-    int nrec = tiling(shapes[v]).n_tiles;
+    int nrec = max_tiles(shapes[v]);
     const int nplain = plain_blocks(nvox, kPlainVpt);      // the plain kernel's records (P = 1)
     if (nplain > nrec) nrec = nplain;
     r.pbase[v] = pb;
@@ -261,6 +273,9 @@ struct Profiler {
 cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!g_prof.on) return nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return nullptr;                              // launches of a graph are not timed here
   std::pair<cudaEvent_t, cudaEvent_t> ev;
   if (!g_prof.spare.empty()) {
     ev = g_prof.spare.back();
@@ -296,59 +311,205 @@ struct BatchVol {
   double* c_out;          // device [P][c] or NULL
 };
 
+// ------------------------------------------------------- stencil plans
+// How one batched stencil launch is cut into work items: particles per item
+// (np) and z-chunks per column tile (every volume of the launch is cut into
+// the same number of chunks, each at least kMinTileZ planes deep).
+struct StencilPlan {
+  int np;
+  int chunks;
+};
+
+long long plan_items(const BatchVol* vols, int n, const StencilPlan& pl) {
+  long long items = 0;
+  for (int v = 0; v < n; ++v)
+    items += static_cast<long long>((vols[v].P + pl.np - 1) / pl.np) *
+             tiling(vols[v].shape, pl.chunks).n_tiles;
+  return items;
+}
+
+int plan_grid(int c, const StencilPlan& pl, long long items) {
+  long long g = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np);
+  if (g > items) g = items;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+int most_chunks(const BatchVol* vols, int n) {
+  int k = 1;
+  for (int v = 0; v < n; ++v)
+    if (max_chunks(vols[v].shape.nz) > k) k = max_chunks(vols[v].shape.nz);
+  return k;
+}
+
+// Built-in choice: the deepest chunks that still give every CTA of the
+// persistent grid at least four items (whole columns when the batch is big
+// enough: fewer halo planes and pipeline fills per voxel).
+StencilPlan heuristic_plan(const BatchVol* vols, int n, int c) {
+  StencilPlan pl{stencil_default_np(c), 1};
+  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np);
+  const int kmax = most_chunks(vols, n);
+  while (pl.chunks < kmax && plan_items(vols, n, pl) < want) ++pl.chunks;
+  return pl;
+}
+
+struct Tuner {
+  std::mutex mu;
+  int mode = 0;
+  StencilPlan force{0, 0};       // np > 0: every launch uses this plan
+  std::map<std::vector<long long>, StencilPlan> cache;
+} g_tune;
+
+// Cache key: element type of the memberships (0 = FP32), c, and every
+// volume's extent and particle count.
+std::vector<long long> plan_key(const BatchVol* vols, int n, int c) {
+  std::vector<long long> k{0, c, n};
+  for (int v = 0; v < n; ++v) {
+    const ifcm_shape& s = vols[v].shape;
+    k.insert(k.end(), {s.nx, s.ny, s.nz, vols[v].P});
+  }
+  return k;
+}
+
+// Parameter block of one iteration kind: 0 reads the shared start U0 and
+// writes ua, 1 reads ua and writes ub, 2 reads ub and writes ua.
+ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_params* p,
+                       const RunBufs& rb, const StencilPlan& pl, int kind, DevStatus* status) {
+  const int c = p->c;
+  std::memset(static_cast<void*>(&a), 0, sizeof(StencilArgs));
+  a.n_vol = n;
+  a.centres = rb.st.centres;
+  a.active = rb.st.active;
+  a.partials = rb.partials;
+  a.dmax = rb.dmax;
+  a.status = status;
+  fill_method(a, p);
+  for (int v = 0; v < n; ++v) {
+    const BatchVol& bv = vols[v];
+    const ifcm_shape& s = bv.shape;
+    const Tiling t = tiling(s, pl.chunks);
+    const size_t plane = plane_elems(s);
+    VolDesc& d = a.vol[v];
+    d.nx = s.nx;
+    d.ny = s.ny;
+    d.nz = s.nz;
+    d.pitch = s.pitch_x;
+    d.tiles_x = t.tiles_x;
+    d.tiles_y = t.tiles_y;
+    d.tz = t.tz;
+    d.n_tiles = t.n_tiles;
+    d.P = bv.P;
+    d.pbase = rb.pbase[v];
+    d.rec_base = rb.rec_base[v];
+    d.lam_xi = bv.lam_xi;
+    const float* src = kind == 0 ? bv.u0 : (kind == 1 ? rb.ua[v] : rb.ub[v]);
+    d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
+    d.u_src = src;
+    d.src_pstride = kind == 0 ? 0 : static_cast<long long>(c) * plane;
+    d.src_cstride = kind == 0 ? 0 : c;
+    ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
+    ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? c : bv.P * c, c));
+  }
+  return IFCM_OK;
+}
+
+// Time every candidate plan on the batch itself: one launch from the shared
+// start (fills ua), then two timed launches ua -> ub, as in any later
+// iteration.  Only the stencil kernel runs, so the run state is untouched
+// and the real run that follows starts from iteration 0 again.
+ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
+                      DevStatus* status, cudaStream_t st, StencilPlan* best) {
+  const int c = p->c;
+  const StencilPlan h = heuristic_plan(vols, n, c);
+  const int kmax = most_chunks(vols, n);
+  std::vector<StencilPlan> cand;
+  for (int np = 1; np <= 2; ++np) {
+    if (!stencil_np_supported(c, np)) continue;
+    for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
+      if (k > kmax) break;
+      const StencilPlan pl{np, k};
+      if (plan_items(vols, n, pl) < sm_count() && k < kmax) continue;
+      cand.push_back(pl);
+    }
+    if (np == h.np && h.chunks > 16) cand.push_back(h);
+  }
+  std::vector<StencilArgs> args(2);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU_TRY(cudaEventCreate(&e0));
+  CU_TRY(cudaEventCreate(&e1));
+  float best_ms = 0.0f;
+  *best = h;
+  ifcm_status rc = IFCM_OK;
+  for (const StencilPlan& pl : cand) {
+    rc = build_args(args[0], vols, n, p, rb, pl, 0, status);
+    if (rc == IFCM_OK) rc = build_args(args[1], vols, n, p, rb, pl, 1, status);
+    if (rc != IFCM_OK) break;
+    const int grid = plan_grid(c, pl, plan_items(vols, n, pl));
+    cudaError_t e = launch_stencil(c, pl.np, args[0], grid, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_stencil(c, pl.np, args[1], grid, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(IFCM_ERR_CUDA, "stencil plan timing: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (best_ms == 0.0f || ms < best_ms) {
+      best_ms = ms;
+      *best = pl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
+                        DevStatus* status, cudaStream_t st, StencilPlan* out) {
+  const std::vector<long long> key = plan_key(vols, n, p->c);
+  int mode;
+  {
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    if (g_tune.force.np > 0 && stencil_np_supported(p->c, g_tune.force.np)) {
+      *out = g_tune.force;
+      return IFCM_OK;
+    }
+    auto it = g_tune.cache.find(key);
+    if (it != g_tune.cache.end()) {
+      *out = it->second;
+      return IFCM_OK;
+    }
+    mode = g_tune.mode;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU_TRY(cudaStreamIsCapturing(st, &cap));
+  if (mode == 0 || cap != cudaStreamCaptureStatusNone) {
+    *out = heuristic_plan(vols, n, p->c);      // a stream being captured is never timed
+    return IFCM_OK;
+  }
+  ST_TRY(tune_plan(vols, n, p, rb, status, st, out));
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  g_tune.cache[key] = *out;
+  return IFCM_OK;
+}
+
 // IFCM runs of every particle of n volumes (same c, n <= kMaxVols) with the
 // stencil kernel: one launch per iteration covers all volumes' work items.
 ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p, RunBufs& rb,
                               DevStatus* status, cudaStream_t st) {
   const int c = p->c;
   int P_total = 0;
-  long long items = 0;
-  const int npi = stencil_particles_per_item(c);
   for (int v = 0; v < n; ++v) {
     CU_TRY(launch_run_init(c, vols[v].P, vols[v].c0, shifted(rb.st, rb.pbase[v], c), nullptr,
                            st));
     P_total += vols[v].P;
-    items += static_cast<long long>((vols[v].P + npi - 1) / npi) * tiling(vols[v].shape).n_tiles;
   }
+  StencilPlan pl;
+  ST_TRY(choose_plan(vols, n, p, rb, status, st, &pl));
   // Three parameter blocks: iteration 0 (U0 -> ua), odd (ua -> ub), even (ub -> ua).
   std::vector<StencilArgs> args(3);
-  for (int k = 0; k < 3; ++k) {
-    StencilArgs& a = args[k];
-    std::memset(static_cast<void*>(&a), 0, sizeof(StencilArgs));
-    a.n_vol = n;
-    a.centres = rb.st.centres;
-    a.active = rb.st.active;
-    a.partials = rb.partials;
-    a.dmax = rb.dmax;
-    a.status = status;
-    fill_method(a, p);
-    for (int v = 0; v < n; ++v) {
-      const BatchVol& bv = vols[v];
-      const ifcm_shape& s = bv.shape;
-      const Tiling t = tiling(s);
-      const size_t pl = plane_elems(s);
-      VolDesc& d = a.vol[v];
-      d.nx = s.nx;
-      d.ny = s.ny;
-      d.nz = s.nz;
-      d.pitch = s.pitch_x;
-      d.tiles_x = t.tiles_x;
-      d.tiles_y = t.tiles_y;
-      d.tz = t.tz;
-      d.n_tiles = t.n_tiles;
-      d.P = bv.P;
-      d.pbase = rb.pbase[v];
-      d.rec_base = rb.rec_base[v];
-      d.lam_xi = bv.lam_xi;
-      const float* src = k == 0 ? bv.u0 : (k == 1 ? rb.ua[v] : rb.ub[v]);
-      d.u_dst = k == 1 ? rb.ub[v] : rb.ua[v];
-      d.u_src = src;
-      d.src_pstride = k == 0 ? 0 : static_cast<long long>(c) * pl;
-      d.src_cstride = k == 0 ? 0 : c;
-      ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
-      ST_TRY(make_map(&a.tm_u[v], src, s, k == 0 ? c : bv.P * c, c));
-    }
-  }
+  for (int k = 0; k < 3; ++k) ST_TRY(build_args(args[k], vols, n, p, rb, pl, k, status));
   ReduceArgs r{};
   r.n_vol = n;
   r.P_total = P_total;
@@ -362,22 +523,19 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
     ReduceVol& rv = r.vol[v];
     rv.pbase = rb.pbase[v];
     rv.P = vols[v].P;
-    rv.n_rec = tiling(vols[v].shape).n_tiles;
+    rv.n_rec = tiling(vols[v].shape, pl.chunks).n_tiles;
     rv.rec_base = rb.rec_base[v];
     rv.nvox = static_cast<long long>(vols[v].shape.nx) * vols[v].shape.ny * vols[v].shape.nz;
     rv.fitness = vols[v].fitness;
     rv.iters_out = vols[v].iters;
     rv.c_out = vols[v].c_out;
   }
-  long long grid = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c);
-  if (grid > items) grid = items;
-  if (grid < 1) grid = 1;
-
+  const int grid = plan_grid(c, pl, plan_items(vols, n, pl));
   for (int it = 0; it < p->max_iter; ++it) {
     const StencilArgs& a = args[it == 0 ? 0 : (it % 2 == 1 ? 1 : 2)];
     cudaEvent_t ev_end = nullptr;
     cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-    CU_TRY(launch_stencil(c, a, static_cast<int>(grid), st));
+    CU_TRY(launch_stencil(c, pl.np, a, grid, st));
     if (ev_beg) cudaEventRecord(ev_end, st);
     CU_TRY(launch_reduce(c, r, st));
   }
@@ -706,6 +864,56 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
 
 }  // extern "C"
 
+// ------------------------------------------------------- plan selection
+extern "C" {
+
+void ifcm_autotune_enable(int32_t mode) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  g_tune.mode = mode ? 1 : 0;
+}
+
+void ifcm_autotune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  g_tune.cache.clear();
+}
+
+ifcm_status ifcm_stencil_force_plan(int32_t np, int32_t chunks) {
+  if (np == 0) {
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    g_tune.force = StencilPlan{0, 0};
+    return IFCM_OK;
+  }
+  if ((np != 1 && np != 2) || chunks < 1)
+    return fail(IFCM_ERR_INVALID, "forced plan np = %d, chunks = %d", np, chunks);
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  g_tune.force = StencilPlan{np, chunks};
+  return IFCM_OK;
+}
+
+int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, int32_t* tz) {
+  if (check_shape(shape) != IFCM_OK || c < 2 || c > kMaxC || P < 1) return -1;
+  BatchVol bv{};
+  bv.shape = shape;
+  bv.P = P;
+  StencilPlan pl = heuristic_plan(&bv, 1, c);
+  int32_t tuned = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    auto it = g_tune.cache.find(plan_key(&bv, 1, c));
+    if (g_tune.force.np > 0 && stencil_np_supported(c, g_tune.force.np)) {
+      pl = g_tune.force;
+    } else if (it != g_tune.cache.end()) {
+      pl = it->second;
+      tuned = 1;
+    }
+  }
+  if (np) *np = pl.np;
+  if (tz) *tz = tiling(shape, pl.chunks).tz;
+  return tuned;
+}
+
+}  // extern "C"
+
 // -------------------------------------------------- pso_fitness_multi
 namespace {
 
@@ -833,7 +1041,57 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
 
 }  // extern "C"
 
+// ------------------------------------------------------------ CUDA graphs
+struct ifcm_graph_t {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
 extern "C" {
+
+ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
+                                    const ifcm_params* p, void* ws, size_t ws_bytes,
+                                    ifcm_graph* out) {
+  if (!out) return fail(IFCM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  ST_TRY(check_multi(vols, n, p));
+  cudaStream_t cs = nullptr;
+  CU_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return fail(IFCM_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  }
+  const ifcm_status rc = pso_fitness_multi(vols, n, p, ws, ws_bytes, cs);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (rc != IFCM_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != IFCM_OK ? rc : fail(IFCM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(IFCM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+  }
+  *out = new ifcm_graph_t{g, ex};
+  return IFCM_OK;
+}
+
+ifcm_status ifcm_graph_launch(ifcm_graph g, void* stream) {
+  if (!g) return fail(IFCM_ERR_INVALID, "graph is NULL");
+  CU_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return IFCM_OK;
+}
+
+void ifcm_graph_destroy(ifcm_graph g) {
+  if (!g) return;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+}
 
 // ------------------------------------------------------------- swarm
 static ifcm_status check_swarm(const pso_state* s) {

@@ -1,750 +1,60 @@
-// Batched IFCM iteration: the neighbourhood stencil of Eqs 5-9 fused with the
-// distance (Eq 4), membership (Eq 2), objective (Eq 1) and centre sums (Eq 3),
-// for every active particle of a batch, in one persistent launch.
-//
-// Work item = (group of NP particles, TX x TY column tile, z-chunk of tz
-// planes).  Warp 8 of each CTA is the producer: one lane walks the CTA's items
-// plane by plane and, for each plane, issues TMA tile loads of the normalised
-// volume x and of the c membership planes U^t of each particle of the group
-// (one-voxel halo in y, aligned four-voxel margins in x) into a ring of
-// shared-memory stages, gated by "full" (transaction bytes) and "empty"
-// (one arrival per consumer warp) mbarriers.  Warps 0-7 are consumers: thread
-// (tx, ty) owns column (x0 + tx, y0 + ty) and keeps four centres of the column
-// in registers.  The plane being consumed contributes to the centre below it
-// (dz = +1), its own centre (dz = 0) and the centre above (dz = -1); the
-// centre two planes below, completed by the previous plane, is finalised in
-// the same step so that its long dependency chain overlaps the stencil
-// arithmetic.  The per-centre sums are float2 pairs (the two particles of an
-// item, or two clusters) updated with packed FP32x2 instructions.  A plane's
-// stage is released once the centre it holds has been finalised:
-// H = sum u g / sum g, F = sum u^2 q^2 / sum q^2 (q^2 = dx^2+dy^2+dz^2,
-// reading R1), Eqs 4 and 2, U^{t+1} written from registers, and the centre's
-// shares of sum u^m, sum u^m x, J and max|du|.
-//
-// Neighbours outside the volume are excluded (reading R4) without masks:
-// the volume's tensor map fills positions outside the volume with NaN and
-// g = max(|x_i - x_k|, 0) turns them into 0 (max ignores a NaN operand),
-// while the membership tensor maps fill them with 0.  Out-of-range planes are
-// never loaded.  The NP particles of a group share the x tile, every g_ik and
-// sum_k g_ik.  Per item and particle, the sums go to a partial record (FP32
-// within a thread and a warp, FP64 across warps) that the reduce kernel sums
-// per particle in FP64.
-#include "ifcm_math.cuh"
-#include "launch.h"
+// The stencil kernel with one particle per work item (every c), and the
+// dispatch over (c, particles per item) used by the run loops.  The kernel
+// itself is in stencil_kernel.cuh; two particles per item (c <= 4) are
+// compiled in ifcm_stencil_np2.cu.
+#include "stencil_kernel.cuh"
 
 namespace pifcm {
 
-namespace {
+// Defined in ifcm_stencil_np2.cu.
+cudaError_t launch_stencil_np2(int c, const StencilArgs& a, int grid, cudaStream_t s);
+int blocks_per_sm_np2(int c);
+size_t smem_bytes_np2(int c);
 
-constexpr int TX = kTX, TY = kTY;
-constexpr int NCW = 8;                 // consumer warps
-constexpr int NCT = NCW * 32;          // consumer threads (one per column of the tile)
-constexpr int NT = NCT + 32;           // + one producer warp
-constexpr int BX = TX + 8;             // x box: 4-voxel aligned margins (TMA x must be 16-B aligned)
-constexpr int BY = TY + 2;             // y box: one-voxel halo
-constexpr int PLANE = BX * BY;         // floats in one channel of a stage
-#ifndef PIFCM_STENCIL_STAGES
-#define PIFCM_STENCIL_STAGES 8
-#endif
-constexpr int NSTAGE = PIFCM_STENCIL_STAGES;   // ring depth
-static_assert(NSTAGE >= 5, "the consumers hold four stages at a time (pz-2 .. pz+1)");
-constexpr int XBYTES = ((PLANE * 4 + 127) / 128) * 128;
-constexpr int CBAR = 1;                // named barrier id of the consumer warps
-
-// Build-time tuning: CTAs per SM the register budget targets, and particles
-// per work item for c <= 4 (c > 4 always uses one).
-#ifndef PIFCM_STENCIL_MIN_BLOCKS
-#define PIFCM_STENCIL_MIN_BLOCKS 1
-#endif
-#ifndef PIFCM_STENCIL_NP_SMALL_C
-#define PIFCM_STENCIL_NP_SMALL_C 2
-#endif
-
-// One particle's c membership planes in a stage, padded so that every TMA
-// destination starts on a 128-byte boundary.
-template <int C>
-__host__ __device__ constexpr int ubytes() {
-  return ((C * PLANE * 4 + 127) / 128) * 128;
-}
-template <int C>
-__host__ __device__ constexpr int ufloats() {
-  return ubytes<C>() / 4;
-}
-template <int C, int NP>
-__host__ __device__ constexpr int stage_bytes() {
-  return XBYTES + NP * ubytes<C>();
-}
-static_assert(XBYTES % 128 == 0 && ubytes<3>() % 128 == 0 && ubytes<5>() % 128 == 0 &&
-                  ubytes<7>() % 128 == 0,
-              "TMA shared-memory destinations must start on 128-byte boundaries");
-template <int C, int NP>
-__host__ __device__ constexpr uint32_t stage_tx_bytes() {
-  return static_cast<uint32_t>((1 + NP * C) * PLANE * 4);
-}
-template <int C, int NP>
-__host__ __device__ constexpr int smem_total() {
-  return NSTAGE * stage_bytes<C, NP>() + 128;
+bool stencil_np_supported(int c, int np) {
+  if (c < 2 || c > kMaxC) return false;
+  return np == 1 || (np == 2 && c <= 4);
 }
 
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync %0, %1;" ::"n"(CBAR), "n"(NCT) : "memory");
-}
+int stencil_default_np(int c) { return c <= 4 ? 2 : 1; }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-// g = |a - b|, and 0 when b is the NaN that marks a position outside the volume.
-__device__ __forceinline__ float gdist(float a, float b) {
-  float r;
-  asm("max.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(fabsf(a - b)));
-  return r;
-}
-
-struct Item {
-  int v;               // volume
-  int p0, p1;          // the volume's particles of the group (p1 = p0 when the group has one)
-  bool two;            // p1 is a distinct particle
-  int tile, x0, y0, z0, z1, pzb, pze;
-};
-
-// Work items of a launch, numbered volume by volume: the active particles of
-// volume v (s_act[vfirst[v] ...], vnact[v] of them) in groups of NP, times the
-// volume's tiles; vitem[v] is the volume's first item.
-struct ItemTable {
-  short act[kMaxBatchParticles];
-  int vfirst[kMaxVols], vnact[kMaxVols], vitem[kMaxVols + 1];
-};
-
-template <int NP>
-__device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTable& tab, int w) {
-  Item it;
-  int v = 0;
-  while (v + 1 < a.n_vol && tab.vitem[v + 1] <= w) ++v;
-  const VolDesc& vd = a.vol[v];
-  it.v = v;
-  const int wl = w - tab.vitem[v];
-  const int g = wl / vd.n_tiles;
-  it.tile = wl - g * vd.n_tiles;
-  const short* act = tab.act + tab.vfirst[v];
-  it.p0 = act[g * NP];
-  it.two = (NP == 2) && (g * NP + 1 < tab.vnact[v]);
-  it.p1 = it.two ? act[g * NP + 1] : it.p0;
-  const int per_z = vd.tiles_x * vd.tiles_y;
-  const int zc = it.tile / per_z;
-  const int rem = it.tile - zc * per_z;
-  const int ty = rem / vd.tiles_x;
-  const int tx = rem - ty * vd.tiles_x;
-  it.x0 = tx * TX;
-  it.y0 = ty * TY;
-  it.z0 = zc * vd.tz;
-  it.z1 = min(it.z0 + vd.tz, vd.nz);
-  it.pzb = max(it.z0 - 1, 0);
-  it.pze = min(it.z1, vd.nz - 1);
-  return it;
-}
-
-// The per-centre sums are kept as float2 pairs and updated with packed FP32x2
-// instructions (half the issue slots of scalar FP32).  With two particles per
-// item, pair k holds cluster k of particle 0 and of particle 1; with one, pair
-// k holds clusters 2k and 2k+1 (the second half of the last pair is unused
-// when c is odd).
-template <int C, int NP>
-struct Pairs {
-  static constexpr int K = NP == 2 ? C : (C + 1) / 2;
-};
-
-template <int C, int NP>
-__device__ __forceinline__ float2 load_pair(const float* __restrict__ us, int k, int off) {
-  if (NP == 2) return make_float2(us[k * PLANE + off], us[ufloats<C>() + k * PLANE + off]);
-  const float lo = us[(2 * k) * PLANE + off];
-  const float hi = (2 * k + 1 < C) ? us[(2 * k + 1) * PLANE + off] : 0.0f;
-  return make_float2(lo, hi);
-}
-
-// Component of (particle p, cluster j) in an array of pairs.
-template <int C, int NP>
-__device__ __forceinline__ float pick(const float2 (&v)[Pairs<C, NP>::K], int p, int j) {
-  if (NP == 2) return p == 0 ? v[j].x : v[j].y;
-  return (j & 1) ? v[j >> 1].y : v[j >> 1].x;
-}
-
-__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-
-// Accumulators of one centre voxel of the column, for NP particles.
-template <int C, int NP>
-struct Slot {
-  static constexpr int K = Pairs<C, NP>::K;
-  float G;            // sum_k g_ik (shared by the particles)
-  float2 H[K];        // sum_k u_kj g_ik
-  float2 F[K];        // sum_k u_kj^2 q^2_ik
-  __device__ __forceinline__ void clear() {
-    G = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) H[k] = F[k] = make_float2(0.0f, 0.0f);
-  }
-};
-
-// A thread's shares of the item's sums: sum u^m and sum u^m x (paired like the
-// slots), J and max|du| per particle.
-template <int C, int NP>
-struct Sums {
-  static constexpr int K = Pairs<C, NP>::K;
-  float2 s0[K], s1[K];
-  float J[NP], dm[NP];
-  __device__ __forceinline__ void clear() {
-#pragma unroll
-    for (int k = 0; k < K; ++k) s0[k] = s1[k] = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) J[p] = dm[p] = 0.0f;
-  }
-};
-
-// Constants of the item being processed, shared by the consumer threads.
-template <int C, int NP>
-struct ItemConst {
-  float2 ncc[Pairs<C, NP>::K];   // minus the centres C^t, paired like the slots
-  float2 nlam, nxi;              // minus lambda and xi of the pair's particles
-  float* dst[NP];                // each particle's U^{t+1}
-};
-
-// Contributions of one plane (x in xs, memberships of particle p at us + p *
-// ufloats<C>()) to the centres below (lo), in (mid) and above (hi) it.  F uses
-// the plane's window sums A = sum w and B = sum (dx^2 + dy^2) w (w = u^2): the
-// planes above and below weigh q^2 = 1 + dx^2 + dy^2 (A + B), the same plane
-// dx^2 + dy^2 (B).
-template <int C, int NP, bool Z3>
-__device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
-                                                 const float* __restrict__ us, int cidx,
-                                                 float x_lo, float x_mid, float x_hi,
-                                                 Slot<C, NP>& lo, Slot<C, NP>& mid,
-                                                 Slot<C, NP>& hi) {
-  constexpr int K = Pairs<C, NP>::K;
-  float2 A[K], B[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) A[k] = B[k] = make_float2(0.0f, 0.0f);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int off = cidx + dy * BX + dx;
-      const float xk = xs[off];
-      const bool self = (dx == 0 && dy == 0);
-      const int q2 = dx * dx + dy * dy;          // folded after unrolling
-      float gl = 0.0f, gh = 0.0f, gm = 0.0f;
-      if (Z3) {
-        gl = gdist(x_lo, xk);
-        gh = gdist(x_hi, xk);
-        lo.G += gl;
-        hi.G += gh;
-      }
-      if (!self) {
-        gm = gdist(x_mid, xk);
-        mid.G += gm;
-      }
-      const float2 gl2 = dup2(gl), gh2 = dup2(gh), gm2 = dup2(gm);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float2 uk = load_pair<C, NP>(us, k, off);
-        if (Z3) {
-          lo.H[k] = __ffma2_rn(uk, gl2, lo.H[k]);
-          hi.H[k] = __ffma2_rn(uk, gh2, hi.H[k]);
-        }
-        if (!self) mid.H[k] = __ffma2_rn(uk, gm2, mid.H[k]);
-        const float2 wk = __fmul2_rn(uk, uk);
-        A[k] = __fadd2_rn(A[k], wk);
-        if (q2 == 1) B[k] = __fadd2_rn(B[k], wk);
-        if (q2 == 2) B[k] = __ffma2_rn(dup2(2.0f), wk, B[k]);
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (Z3) {
-      const float2 ab = __fadd2_rn(A[k], B[k]);
-      lo.F[k] = __fadd2_rn(lo.F[k], ab);
-      hi.F[k] = __fadd2_rn(hi.F[k], ab);
-    }
-    mid.F[k] = __fadd2_rn(mid.F[k], B[k]);
-  }
-}
-
-// Per-item position of one consumer thread's column.
-struct Ctx {
-  int X, Y;
-  bool col_ok, col_interior;
-  int col_off;                 // Y * pitch + X
-};
-
-__device__ __forceinline__ float2 max2(float2 v, float lo) {
-  return make_float2(fmaxf(v.x, lo), fmaxf(v.y, lo));
-}
-
-// Finalise one centre (its u^t is read from its plane's stage at cus): H and F
-// (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
-// the centre's shares of Eqs 1 and 3, in packed pairs.
-template <int C, int NP>
-__device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
-                                                int cidx, float xc, int z, bool interior,
-                                                const VolDesc& a, const Item& it,
-                                                const ItemConst<C, NP>& ic, const Ctx& cx,
-                                                const MethodConsts& k, Sums<C, NP>& acc) {
-  constexpr int K = Pairs<C, NP>::K;
-  float invQ;
-  int cnt = 1;
-  if (interior) {
-    invQ = a.nz > 1 ? (1.0f / 54.0f) : (1.0f / 12.0f);
-  } else {
-    float Q;
-    box_counts(cx.X, cx.Y, z, a.nx, a.ny, a.nz, cnt, Q);
-    invQ = cnt > 0 ? __frcp_rn(Q) : 0.0f;
-  }
-  float2 H[K], F[K];
-  if (cnt == 0) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) H[q] = F[q] = make_float2(0.0f, 0.0f);
-  } else {
-    const float2 iq = dup2(invQ);
-#pragma unroll
-    for (int q = 0; q < K; ++q) F[q] = __fmul2_rn(sl.F[q], iq);
-    if (sl.G >= 1.0e-30f) {
-      const float2 ig = dup2(fast_rcp(sl.G));
-#pragma unroll
-      for (int q = 0; q < K; ++q) H[q] = __fmul2_rn(sl.H[q], ig);
-    } else if (sl.G > 0.0f) {
-      const float2 ig = dup2(__frcp_rn(sl.G));
-#pragma unroll
-      for (int q = 0; q < K; ++q) H[q] = __fmul2_rn(sl.H[q], ig);
-    } else {   // every neighbour equals x_i: plain mean of u_kj (reading R3)
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const int pid = p == 0 ? it.p0 : it.p1;
-        float Hm[C];
-        flat_neighbourhood_mean<C>(a.u_src + static_cast<long long>(pid) * a.src_pstride, cx.X,
-                                   cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          if (NP == 2) {
-            if (p == 0) H[j].x = Hm[j];
-            else H[j].y = Hm[j];
-          } else if (j & 1) {
-            H[j >> 1].y = Hm[j];
-          } else {
-            H[j >> 1].x = Hm[j];
-            if (j == C - 1) H[j >> 1].y = 0.0f;
-          }
-        }
-      }
-    }
-  }
-  // Eq 4 with reading R2
-  const float2 one2 = dup2(1.0f), xc2 = dup2(xc);
-  float2 d2[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const float2 fac =
-        max2(__ffma2_rn(ic.nxi, F[q], __ffma2_rn(ic.nlam, H[q], one2)), 0.0f);
-    const float2 dd = __fadd2_rn(xc2, ic.ncc[q]);
-    d2[q] = max2(__fmul2_rn(__fmul2_rn(dd, dd), fac), k.dist_floor);
-  }
-  // Eq 2
-  float2 u[K], um[K];
-  if (k.m_is_2) {
-    float2 r[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) r[q] = make_float2(fast_rcp(d2[q].x), fast_rcp(d2[q].y));
-    float2 inv;
-    if (NP == 2) {
-      float2 S = r[0];
-#pragma unroll
-      for (int q = 1; q < K; ++q) S = __fadd2_rn(S, r[q]);
-      inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
-      acc.J[0] += inv.x;                       // sum_j u_j^2 d2_j = 1/S
-      acc.J[NP - 1] += inv.y;
-    } else {
-      float S = 0.0f;
-#pragma unroll
-      for (int q = 0; q < K; ++q) S += (2 * q + 1 < C) ? r[q].x + r[q].y : r[q].x;
-      inv = dup2(fast_rcp(S));
-      acc.J[0] += inv.x;
-    }
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      u[q] = __fmul2_rn(r[q], inv);
-      um[q] = __fmul2_rn(u[q], u[q]);
-    }
-  } else {
-    float Sp[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) Sp[p] = 0.0f;
-    float av[NP][C];
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        av[p][j] = exp2f(-k.inv_m1 * log2f(pick<C, NP>(d2, p, j)));
-        Sp[p] += av[p][j];
-      }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float invS = fast_rcp(Sp[p]);
-      float Jv = 0.0f;
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const float uj = av[p][j] * invS;
-        const float umj = exp2f(k.m * log2f(uj));
-        Jv += umj * pick<C, NP>(d2, p, j);
-        if (NP == 2) {
-          if (p == 0) { u[j].x = uj; um[j].x = umj; }
-          else { u[j].y = uj; um[j].y = umj; }
-        } else if (j & 1) {
-          u[j >> 1].y = uj; um[j >> 1].y = umj;
-        } else {
-          u[j >> 1].x = uj; um[j >> 1].x = umj;
-          if (j == C - 1) { u[j >> 1].y = 0.0f; um[j >> 1].y = 0.0f; }
-        }
-      }
-      acc.J[p] += Jv;
-    }
-  }
-  // Eq 3 shares, max|du|, and the store of U^{t+1}
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    acc.s0[q] = __fadd2_rn(acc.s0[q], um[q]);
-    acc.s1[q] = __ffma2_rn(um[q], xc2, acc.s1[q]);
-  }
-  const int plane = a.nz * a.ny * a.pitch;              // c * plane < 2^31 (host-checked)
-  const int voff = z * (a.ny * a.pitch) + cx.col_off;
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    if (p == 1 && !it.two) break;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const float uj = pick<C, NP>(u, p, j);
-      ic.dst[p][j * plane + voff] = uj;
-      acc.dm[p] = fmaxf(acc.dm[p], fabsf(uj - cus[p * ufloats<C>() + j * PLANE + cidx]));
-    }
-  }
-}
-
-template <int C, int NP>
-__global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
-    stencil_kernel(const __grid_constant__ StencilArgs a) {
-  extern __shared__ unsigned char dsmem_raw[];
-  __shared__ __align__(8) uint64_t full[NSTAGE];
-  __shared__ __align__(8) uint64_t empty[NSTAGE];
-  __shared__ ItemTable tab;
-  __shared__ int s_abort;
-  __shared__ float s_red[NCW][NP * (2 * C + 2)];
-  __shared__ ItemConst<C, NP> s_ic;
-
-  unsigned char* dsmem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(dsmem_raw) + 127) & ~static_cast<uintptr_t>(127));
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-
-  // Active particles of every volume, compacted one volume per warp (ballots).
-  for (int v = warp; v < a.n_vol; v += NT / 32) {
-    const VolDesc& vd = a.vol[v];
-    int n = 0;
-    for (int base = 0; base < vd.P; base += 32) {
-      const int p = base + lane;
-      const bool on = p < vd.P && a.active[vd.pbase + p] != 0;
-      const unsigned m = __ballot_sync(0xffffffffu, on);
-      if (on) tab.act[vd.pbase + n + __popc(m & ((1u << lane) - 1u))] = static_cast<short>(p);
-      n += __popc(m);
-    }
-    if (lane == 0) {
-      tab.vfirst[v] = vd.pbase;
-      tab.vnact[v] = n;
-    }
-  }
-  if (tid == 0) {
-    s_abort = 0;
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NCW);
-    }
-    fence_mbarrier_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int items = 0;
-    for (int v = 0; v < a.n_vol; ++v) {
-      tab.vitem[v] = items;
-      items += ((tab.vnact[v] + NP - 1) / NP) * a.vol[v].n_tiles;
-    }
-    tab.vitem[a.n_vol] = items;
-  }
-  __syncthreads();
-  const int n_items = tab.vitem[a.n_vol];
-  if (static_cast<int>(blockIdx.x) >= n_items) return;
-
-  auto xs_of = [&](int s) { return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP>()); };
-  auto us_of = [&](int s) {
-    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP>() + XBYTES);
-  };
-
-  // ------------------------------------------------------------ producer
-  if (warp == NCW) {
-    if (lane == 0) {
-      int q = 0;
-      for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const Item it = decode_item<NP>(a, tab, w);
-        const VolDesc& vd = a.vol[it.v];
-        const CUtensorMap* mx = &a.tm_x[it.v];
-        const CUtensorMap* mu = &a.tm_u[it.v];
-        for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
-          const int s = q % NSTAGE;
-          if (q >= NSTAGE &&
-              !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((q / NSTAGE) - 1) & 1))) {
-            atomicExch(&s_abort, 1);
-            set_status(a.status, IFCM_ERR_TIMEOUT, 3);
-            return;
-          }
-          if (*reinterpret_cast<volatile int*>(&s_abort)) return;
-          mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP>());
-          tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
-          tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                      it.p0 * vd.src_cstride);
-          if (NP == 2)
-            tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                        it.p1 * vd.src_cstride);
-        }
-      }
-    }
-    return;
-  }
-
-  // ------------------------------------------------------------ consumers
-  const int tx = tid & 31, ty = tid >> 5;
-  const int cidx = (ty + 1) * BX + tx + 4;     // the column's position in a stage plane
-  MethodConsts k;
-  k.dist_floor = a.dist_floor;
-  k.m = a.m;
-  k.inv_m1 = a.inv_m1;
-  k.m_is_2 = a.m_is_2;
-  int q = 0;
-
-  // Waits for plane qq's stage (bounded; after a timeout every wait is skipped
-  // so that all consumer threads still reach the same barriers).
-  auto wait_full = [&](int qq) -> bool {
-    if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
-    if (!mbar_wait_bounded(&full[qq % NSTAGE], static_cast<uint32_t>((qq / NSTAGE) & 1))) {
-      atomicExch(&s_abort, 1);
-      set_status(a.status, IFCM_ERR_TIMEOUT, 4);
-      return false;
-    }
-    return true;
-  };
-  auto release = [&](int qq) {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[qq % NSTAGE]);
-  };
-
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const Item it = decode_item<NP>(a, tab, w);
-    const VolDesc& vd = a.vol[it.v];
-    const bool z3 = vd.nz > 1;
-    const int plane = vd.nz * vd.ny * vd.pitch;
-    Ctx cx;
-    cx.X = it.x0 + tx;
-    cx.Y = it.y0 + ty;
-    cx.col_ok = (cx.X < vd.nx) && (cx.Y < vd.ny);
-    cx.col_interior = cx.X > 0 && cx.X < vd.nx - 1 && cx.Y > 0 && cx.Y < vd.ny - 1;
-    cx.col_off = cx.Y * vd.pitch + cx.X;
-    if (tid == 0) {
-      float lam[2], xi[2], cc[2][C];
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int pid = (p == 0 || NP == 1) ? it.p0 : it.p1;
-        lam[p] = static_cast<float>(vd.lam_xi[2 * pid]);
-        xi[p] = static_cast<float>(vd.lam_xi[2 * pid + 1]);
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-          cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
-        if (p < NP) s_ic.dst[p] = vd.u_dst + static_cast<size_t>(pid) * C * plane;
-      }
-      s_ic.nlam = make_float2(-lam[0], -lam[1]);
-      s_ic.nxi = make_float2(-xi[0], -xi[1]);
-#pragma unroll
-      for (int qk = 0; qk < Pairs<C, NP>::K; ++qk) {
-        if (NP == 2) s_ic.ncc[qk] = make_float2(-cc[0][qk], -cc[1][qk]);
-        else s_ic.ncc[qk] = make_float2(-cc[0][2 * qk], 2 * qk + 1 < C ? -cc[0][2 * qk + 1] : 0.0f);
-      }
-    }
-    consumer_sync();
-    Slot<C, NP> sd, sl, sm, sh;
-    sd.clear();
-    sl.clear();
-    sm.clear();
-    sh.clear();
-    Sums<C, NP> acc;
-    acc.clear();
-    const int np = it.pze - it.pzb + 1;
-    const int q0 = q;
-
-    // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1 while
-    // plane pz is consumed.  The centre completed by plane pz - 1 is finalised
-    // in the same basic block as plane pz's stencil so that its dependency
-    // chain (Eqs 4 and 2) overlaps the stencil arithmetic.
-    for (int kk = 0; kk < np; ++kk) {
-      const int qq = q0 + kk;
-      const int pz = it.pzb + kk;
-      const bool has_next = kk + 1 < np;
-      const bool ok = wait_full(qq) && (!has_next || wait_full(qq + 1));
-      if (ok) {
-        const float* xs = xs_of(qq % NSTAGE);
-        const float* us = us_of(qq % NSTAGE);
-        const float x_mid = xs[cidx];
-        const float x_lo = kk > 0 ? xs_of((qq + NSTAGE - 1) % NSTAGE)[cidx] : 0.0f;
-        const float x_hi = has_next ? xs_of((qq + 1) % NSTAGE)[cidx] : 0.0f;
-        const int zd = pz - 2;
-        if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
-          const int sdi = (qq + NSTAGE - 2) % NSTAGE;
-          finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
-                                 cx.col_interior && zd > 0 && zd < vd.nz - 1, vd, it, s_ic, cx,
-                                 k, acc);
-        }
-        if (z3)
-          accumulate_plane<C, NP, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-        else
-          accumulate_plane<C, NP, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-      }
-      if (kk >= 2) release(qq - 2);
-      sd = sl;
-      sl = sm;
-      sm = sh;
-      sh.clear();
-    }
-    // After the last plane: sd = centre pze - 1 (complete) and sl = centre pze
-    // (complete only when pze is the last plane of the volume).
-    {
-      const int ql = q0 + np - 1;
-      const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
-      if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
-        const int sdi = (ql + NSTAGE - 1) % NSTAGE;
-        finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
-                               cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
-                               it, s_ic, cx, k, acc);
-      }
-      if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
-        const int sli = ql % NSTAGE;
-        finalize_centre<C, NP>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
-                               cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
-      }
-      if (np >= 2) release(ql - 1);
-      release(ql);
-    }
-    q = q0 + np;
-
-    // Item partial sums: FP32 within a thread and a warp, FP64 across warps.
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const float v0 = warp_sum(pick<C, NP>(acc.s0, p, j));
-        const float v1 = warp_sum(pick<C, NP>(acc.s1, p, j));
-        if (lane == 0) {
-          s_red[warp][p * (2 * C + 2) + j] = v0;
-          s_red[warp][p * (2 * C + 2) + C + j] = v1;
-        }
-      }
-      const float vj = warp_sum(acc.J[p]);
-      const float vm = warp_max(acc.dm[p]);
-      if (lane == 0) {
-        s_red[warp][p * (2 * C + 2) + 2 * C] = vj;
-        s_red[warp][p * (2 * C + 2) + 2 * C + 1] = vm;
-      }
-    }
-    consumer_sync();
-    if (tid < NP * (2 * C + 2)) {
-      const int p = tid / (2 * C + 2), v = tid - p * (2 * C + 2);
-      if (p == 0 || it.two) {
-        const int pid = p == 0 ? it.p0 : it.p1;
-        const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
-        if (v < 2 * C + 1) {
-          double sum = 0.0;
-#pragma unroll
-          for (int wv = 0; wv < NCW; ++wv) sum += static_cast<double>(s_red[wv][tid]);
-          a.partials[rec * (2 * C + 1) + v] = sum;
-        } else {
-          float mm = 0.0f;
-#pragma unroll
-          for (int wv = 0; wv < NCW; ++wv) mm = fmaxf(mm, s_red[wv][tid]);
-          a.dmax[rec] = mm;
-        }
-      }
-    }
-    consumer_sync();
-  }
-}
-// ---------------------------------------------------------------------------
-template <int C, int NP>
-cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
-  constexpr int smem = smem_total<C, NP>();
-  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  stencil_kernel<C, NP><<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int C, int NP>
-int blocks_per_sm_c() {
-  int n = 0;
-  constexpr int smem = smem_total<C, NP>();
-  cudaFuncSetAttribute(stencil_kernel<C, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP>, NT, smem) !=
-      cudaSuccess)
-    return 1;
-  return n > 0 ? n : 1;
-}
-
-// Particles per item: PIFCM_STENCIL_NP_SMALL_C for c <= 4, one above.
-template <int C>
-constexpr int np_for() {
-  return C <= 4 ? PIFCM_STENCIL_NP_SMALL_C : 1;
-}
-
-}  // namespace
-
-int stencil_particles_per_item(int c) { return c <= 4 ? PIFCM_STENCIL_NP_SMALL_C : 1; }
-
-size_t stencil_smem_bytes(int c) {
+size_t stencil_smem_bytes(int c, int np) {
+  if (np == 2) return smem_bytes_np2(c);
   switch (c) {
-    case 2: return smem_total<2, np_for<2>()>();
-    case 3: return smem_total<3, np_for<3>()>();
-    case 4: return smem_total<4, np_for<4>()>();
-    case 5: return smem_total<5, np_for<5>()>();
-    case 6: return smem_total<6, np_for<6>()>();
-    case 7: return smem_total<7, np_for<7>()>();
-    default: return smem_total<8, np_for<8>()>();
+    case 2: return smem_total<2, 1>();
+    case 3: return smem_total<3, 1>();
+    case 4: return smem_total<4, 1>();
+    case 5: return smem_total<5, 1>();
+    case 6: return smem_total<6, 1>();
+    case 7: return smem_total<7, 1>();
+    default: return smem_total<8, 1>();
   }
 }
 
-int stencil_blocks_per_sm(int c) {
+int stencil_blocks_per_sm(int c, int np) {
+  if (np == 2) return blocks_per_sm_np2(c);
   switch (c) {
-    case 2: return blocks_per_sm_c<2, np_for<2>()>();
-    case 3: return blocks_per_sm_c<3, np_for<3>()>();
-    case 4: return blocks_per_sm_c<4, np_for<4>()>();
-    case 5: return blocks_per_sm_c<5, np_for<5>()>();
-    case 6: return blocks_per_sm_c<6, np_for<6>()>();
-    case 7: return blocks_per_sm_c<7, np_for<7>()>();
-    default: return blocks_per_sm_c<8, np_for<8>()>();
+    case 2: return blocks_per_sm_c<2, 1>();
+    case 3: return blocks_per_sm_c<3, 1>();
+    case 4: return blocks_per_sm_c<4, 1>();
+    case 5: return blocks_per_sm_c<5, 1>();
+    case 6: return blocks_per_sm_c<6, 1>();
+    case 7: return blocks_per_sm_c<7, 1>();
+    default: return blocks_per_sm_c<8, 1>();
   }
 }
 
-cudaError_t launch_stencil(int c, const StencilArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_stencil(int c, int np, const StencilArgs& a, int grid, cudaStream_t s) {
+  if (!stencil_np_supported(c, np)) return cudaErrorInvalidValue;
+  if (np == 2) return launch_stencil_np2(c, a, grid, s);
   switch (c) {
-    case 2: return launch_c<2, np_for<2>()>(a, grid, s);
-    case 3: return launch_c<3, np_for<3>()>(a, grid, s);
-    case 4: return launch_c<4, np_for<4>()>(a, grid, s);
-    case 5: return launch_c<5, np_for<5>()>(a, grid, s);
-    case 6: return launch_c<6, np_for<6>()>(a, grid, s);
-    case 7: return launch_c<7, np_for<7>()>(a, grid, s);
-    case 8: return launch_c<8, np_for<8>()>(a, grid, s);
+    case 2: return launch_c<2, 1>(a, grid, s);
+    case 3: return launch_c<3, 1>(a, grid, s);
+    case 4: return launch_c<4, 1>(a, grid, s);
+    case 5: return launch_c<5, 1>(a, grid, s);
+    case 6: return launch_c<6, 1>(a, grid, s);
+    case 7: return launch_c<7, 1>(a, grid, s);
+    case 8: return launch_c<8, 1>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -12,8 +12,12 @@ namespace pifcm {
 
 // ------------------------------------------------ stencil iteration (batched)
 // Tile of one stencil work item: TX x TY columns of voxels marched along z.
+// kTY rows = kTY consumer warps (+ one producer warp) per CTA.
+#ifndef PIFCM_STENCIL_TY
+#define PIFCM_STENCIL_TY 11
+#endif
 constexpr int kTX = 32;
-constexpr int kTY = 8;
+constexpr int kTY = PIFCM_STENCIL_TY;
 constexpr int kThreads = kTX * kTY;
 
 // One volume of a stencil launch.  A launch covers up to kMaxVols volumes of
@@ -52,10 +56,12 @@ struct StencilArgs {
 };
 static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
 
-int stencil_particles_per_item(int c);   // particles sharing one work item
-size_t stencil_smem_bytes(int c);
-int stencil_blocks_per_sm(int c);
-cudaError_t launch_stencil(int c, const StencilArgs& a, int grid, cudaStream_t s);
+// np = particles sharing one work item: 1 for every c, 2 for c <= 4.
+bool stencil_np_supported(int c, int np);
+int stencil_default_np(int c);
+size_t stencil_smem_bytes(int c, int np);
+int stencil_blocks_per_sm(int c, int np);
+cudaError_t launch_stencil(int c, int np, const StencilArgs& a, int grid, cudaStream_t s);
 
 // ------------------------------------- plain iteration (one thread per voxel)
 struct PlainArgs {

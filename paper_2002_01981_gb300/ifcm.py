@@ -165,6 +165,76 @@ def pso_fitness_batch(x, params, lam_xi, u0, c0, nx=None, ws=None, want_centres=
     return fit, its, cout
 
 
+class FitnessGraph:
+    """A captured ``pso_fitness_multi`` call.  ``launch()`` replays it on the
+    current stream with whatever the input tensors hold then; ``outputs`` are
+    the (fitness, iterations) tensors every replay rewrites."""
+
+    def __init__(self, handle, keep, outputs, ws):
+        self._h = handle
+        self._keep = keep
+        self.outputs = outputs
+        self.ws = ws
+
+    def launch(self):
+        N.check(N.load().ifcm_graph_launch(self._h, _stream()))
+
+    def check(self):
+        """Synchronise and raise if a kernel of the last replay flagged an error."""
+        N.check(device_status(self.ws))
+
+    def close(self):
+        if self._h:
+            N.load().ifcm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pso_fitness_multi_graph(volumes, params, ws=None):
+    """Capture ``pso_fitness_multi(volumes, params)`` into a CUDA graph."""
+    lib = N.load()
+    descs, keep, outs = _multi_descriptors(volumes)
+    p = params.native()
+    dev = volumes[0].x.device
+    if ws is None:
+        ws = workspace(lib.pso_fitness_multi_workspace_bytes(descs, len(volumes),
+                                                             ctypes.byref(p)), dev)
+    h = ctypes.c_void_p()
+    N.check(lib.pso_fitness_multi_graph(descs, len(volumes), ctypes.byref(p), _ptr(ws),
+                                        ws.numel(), ctypes.byref(h)))
+    return FitnessGraph(h, (keep, volumes), outs, ws)
+
+
+# ------------------------------------------------ work decomposition plans
+def autotune(mode=1):
+    """Turn timing of candidate stencil plans on (1) or off (0, built-in rule)."""
+    N.load().ifcm_autotune_enable(int(mode))
+
+
+def autotune_reset():
+    N.load().ifcm_autotune_reset()
+
+
+def force_plan(np_=0, chunks=1):
+    """Make every later launch use np_ particles per item and `chunks`
+    z-chunks per tile (np_ = 0 lifts it)."""
+    N.check(N.load().ifcm_stencil_force_plan(int(np_), int(chunks)))
+
+
+def stencil_plan(shape, c, P):
+    """(particles per item, z-chunk depth, tuned?) for a one-volume batch."""
+    np_, tz = ctypes.c_int32(), ctypes.c_int32()
+    r = N.load().ifcm_stencil_plan(shape, int(c), int(P), ctypes.byref(np_), ctypes.byref(tz))
+    if r < 0:
+        raise ValueError("invalid shape, c or P")
+    return np_.value, tz.value, bool(r)
+
+
 # ------------------------------- Alg 1 step 4, many swarms on many volumes
 @dataclass
 class BatchVolume:

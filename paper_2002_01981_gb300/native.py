@@ -75,6 +75,16 @@ SIGNATURES = {
                                                          POINTER(IfcmParams)]),
     "pso_fitness_multi": (c_int32, [POINTER(IfcmBatchVolume), c_int32, POINTER(IfcmParams),
                                     c_void_p, c_size_t, c_void_p]),
+    "ifcm_autotune_enable": (None, [c_int32]),
+    "ifcm_autotune_reset": (None, []),
+    "ifcm_stencil_force_plan": (c_int32, [c_int32, c_int32]),
+    "ifcm_stencil_plan": (c_int32, [IfcmShape, c_int32, c_int32, POINTER(c_int32),
+                                    POINTER(c_int32)]),
+    "pso_fitness_multi_graph": (c_int32, [POINTER(IfcmBatchVolume), c_int32,
+                                          POINTER(IfcmParams), c_void_p, c_size_t,
+                                          POINTER(c_void_p)]),
+    "ifcm_graph_launch": (c_int32, [c_void_p, c_void_p]),
+    "ifcm_graph_destroy": (None, [c_void_p]),
     "pso_init": (c_int32, [POINTER(PsoState), c_void_p]),
     "pso_step": (c_int32, [POINTER(PsoState), c_void_p, c_void_p]),
     "pifcm3d_workspace_bytes": (c_size_t, [IfcmShape, POINTER(IfcmParams),

@@ -197,3 +197,29 @@ def test_multi_volume_workspace_is_the_largest_wave(lib):
     pc = _params(c=3)
     single = lib.pso_fitness_batch_workspace_bytes(shp, ctypes.byref(pc), 6)
     assert abs(one(a) - single) <= 4096
+
+
+def test_stencil_plan_rule_and_forcing(lib):
+    from paper_2002_01981_gb300 import native as N
+    npp, tz = ctypes.c_int32(), ctypes.c_int32()
+    shp = N.IfcmShape(181, 217, 181, 184)
+    assert lib.ifcm_stencil_plan(shp, 4, 20, ctypes.byref(npp), ctypes.byref(tz)) == 0
+    assert npp.value == 2 and 8 <= tz.value <= 181
+    assert lib.ifcm_stencil_plan(shp, 6, 20, ctypes.byref(npp), ctypes.byref(tz)) == 0
+    assert npp.value == 1
+    assert lib.ifcm_stencil_plan(shp, 9, 20, ctypes.byref(npp), ctypes.byref(tz)) == -1
+    assert lib.ifcm_stencil_plan(N.IfcmShape(5, 4, 3, 6), 4, 20, None, None) == -1
+    # forcing: chunks are clamped to >= 8 planes; np = 2 is ignored above c = 4
+    assert lib.ifcm_stencil_force_plan(3, 1) == 1
+    assert lib.ifcm_stencil_force_plan(1, 0) == 1
+    assert lib.ifcm_stencil_force_plan(1, 100) == 0
+    lib.ifcm_stencil_plan(shp, 4, 20, ctypes.byref(npp), ctypes.byref(tz))
+    assert (npp.value, tz.value) == (1, 8)
+    assert lib.ifcm_stencil_force_plan(2, 4) == 0
+    lib.ifcm_stencil_plan(shp, 4, 20, ctypes.byref(npp), ctypes.byref(tz))
+    assert (npp.value, tz.value) == (2, 46)
+    lib.ifcm_stencil_plan(shp, 5, 20, ctypes.byref(npp), ctypes.byref(tz))
+    assert npp.value == 1
+    assert lib.ifcm_stencil_force_plan(0, 0) == 0
+    lib.ifcm_stencil_plan(N.IfcmShape(64, 64, 1, 64), 4, 1, ctypes.byref(npp), ctypes.byref(tz))
+    assert tz.value == 1

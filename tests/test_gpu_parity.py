@@ -402,3 +402,71 @@ def test_fitness_multi_beyond_one_launch(G):
         f1, i1, _ = G.pso_fitness_batch(v.x, G.Params(c=3, max_iter=4, eps_u=0.0), v.lam_xi,
                                         v.u0, v.c0, nx=v.nx)
         assert torch.equal(fit, f1) and torch.equal(its, i1)
+
+
+# ------------------------------------------------ work decomposition plans
+@pytest.mark.parametrize("c,np_,chunks", [(4, 1, 1), (4, 2, 1), (4, 1, 3), (4, 2, 100),
+                                          (3, 1, 2), (6, 1, 1), (6, 1, 100), (2, 2, 4)])
+def test_every_plan_matches_oracle(G, c, np_, chunks):
+    # z = 37 planes: up to five chunks (the last one ragged), x and y tails too
+    shape = (37, 30, 70)
+    x = unit_volume(shape, seed=121)
+    U0 = phantoms.random_memberships(shape, c, seed=122)
+    C0 = np.sort(np.random.default_rng(123).random(c))
+    lam_xi = np.random.default_rng(124).random((3, 2)) * 0.6
+    G.force_plan(np_, chunks)
+    try:
+        fit, its, cout = G.pso_fitness_batch(dev_vol(x), G.Params(c=c, max_iter=6, eps_u=0.0),
+                                             lam_xi, dev_u(U0), C0, nx=shape[2],
+                                             want_centres=True)
+    finally:
+        G.force_plan(0)
+    fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
+                              max_iter=6, eps=0.0)
+    assert np.array_equal(its.cpu().numpy(), io)
+    assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
+
+
+def test_autotuned_plan_is_cached_and_matches_oracle(G):
+    shape = (24, 40, 70)
+    x = unit_volume(shape, seed=131)
+    U0 = phantoms.random_memberships(shape, 4, seed=132)
+    C0 = np.array([0.1, 0.35, 0.6, 0.85])
+    lam_xi = np.random.default_rng(133).random((5, 2)) * 0.6
+    xg = dev_vol(x)
+    G.autotune_reset()
+    G.autotune(1)
+    try:
+        fit, its, _ = G.pso_fitness_batch(xg, G.Params(c=4, max_iter=5, eps_u=0.0), lam_xi,
+                                          dev_u(U0), C0, nx=shape[2])
+        npp, tz, tuned = G.stencil_plan(G.shape_of(xg, shape[2]), 4, 5)
+    finally:
+        G.autotune(0)
+        G.autotune_reset()
+    assert tuned and npp in (1, 2) and 8 <= tz <= 24
+    fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
+                              max_iter=5, eps=0.0)
+    assert np.array_equal(its.cpu().numpy(), io)
+    assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
+
+
+def test_fitness_graph_replays_follow_the_inputs(G):
+    vols, _ = _multi_inputs(G, MULTI_SPECS, seed=141)
+    for v in vols:
+        v.lam_xi = torch.tensor(v.lam_xi, dtype=torch.float64, device="cuda")
+    prm = G.Params(max_iter=7, eps_u=1e-5)
+    graph = G.pso_fitness_multi_graph(vols, prm)
+    try:
+        for trial in range(2):
+            if trial:
+                for k, v in enumerate(vols):       # the swarm moves: new values, same buffers
+                    v.lam_xi.copy_(torch.rand(v.lam_xi.shape, dtype=torch.float64,
+                                              generator=torch.Generator().manual_seed(k))
+                                   .cuda())
+            graph.launch()
+            graph.check()
+            direct = G.pso_fitness_multi(vols, prm)
+            for (fg, ig), (fd, id_) in zip(graph.outputs, direct):
+                assert torch.equal(fg, fd) and torch.equal(ig, id_)
+    finally:
+        graph.close()
