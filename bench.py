@@ -190,6 +190,73 @@ def plain_form_rate(G, vol, nx, prm, opts, stream, particles=2):
                       f"host stop test per iteration), plain kernel, same volume"}
 
 
+# ------------------------------------------------- many volumes at once
+BATCH_VOLUMES = 48
+BATCH_P = 32
+BATCH_BUDGET = 48 << 30            # workspace bytes: the c = 5 and c = 6 groups take two waves
+BATCH_WORKLOAD = (f"{BATCH_VOLUMES} phantoms of uneven size (each side U{{64..224}}), c U{{4,5,6}}, "
+                  f"Rician sigma 0.03/0.07/0.12, {BATCH_P} particles each, <= {MAX_ITER} IFCM "
+                  f"iterations per fitness, stop max|du|<{EPS:g}")
+
+
+def batching_leg(G, phantoms, dev):
+    """Fitness of every particle of every volume of the uneven batch: the
+    captured multi-volume call (volumes of one c share each launch) against
+    one pso_fitness_batch call per volume, both on the same workspace."""
+    import torch
+    vols, nvox = [], []
+    for k, (raw, c) in enumerate(phantoms.uneven_volumes(BATCH_VOLUMES, seed=3)):
+        nz, ny, nx = raw.shape
+        v = torch.from_numpy(phantoms.pad_pitch(raw)).to(dev)
+        x = G.ifcm_normalize(v, nx=nx)
+        U0, C0, _, _ = G.ifcm_fit(x, G.Params(c=c, m=M, max_iter=INIT_MAX_ITER, eps_u=EPS),
+                                  (0.0, 0.0), nx=nx)
+        lam = torch.rand((BATCH_P, 2), generator=torch.Generator().manual_seed(k),
+                         dtype=torch.float64).to(dev)
+        vols.append(G.BatchVolume(x, c, lam, U0, C0, nx=nx))
+        nvox.append(nz * ny * nx)
+    prm = G.Params(m=M, max_iter=MAX_ITER, eps_u=EPS)
+    ws = G.workspace(BATCH_BUDGET, dev)
+    waves = G.pso_fitness_multi_waves(vols, prm, ws.numel())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    graph = G.pso_fitness_multi_graph(vols, prm, ws=ws)
+    graph.launch()
+    graph.check()
+    torch.cuda.synchronize()
+    ev0.record()
+    graph.launch()
+    ev1.record()
+    graph.check()
+    ms_batched = ev0.elapsed_time(ev1)
+    updates = sum(int(its.sum()) * n for (_, its), n in zip(graph.outputs, nvox))
+    graph.close()
+
+    torch.cuda.synchronize()
+    ev0.record()
+    loop_updates = 0
+    for v, n in zip(vols, nvox):
+        _, its, _ = G.pso_fitness_batch(v.x, G.Params(c=v.c, m=M, max_iter=MAX_ITER, eps_u=EPS),
+                                        v.lam_xi, v.u0, v.c0, nx=v.nx, ws=ws)
+        loop_updates += int(its.sum()) * n
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_loop = ev0.elapsed_time(ev1)
+    del ws, vols
+    torch.cuda.empty_cache()
+    batched = updates / (ms_batched / 1e3)
+    loop = loop_updates / (ms_loop / 1e3)
+    return {"workload": BATCH_WORKLOAD, "volumes": BATCH_VOLUMES,
+            "particles": BATCH_VOLUMES * BATCH_P, "voxels": int(sum(nvox)),
+            "workspace_bytes": BATCH_BUDGET, "waves": waves,
+            "batched_graph": {"value": batched, "unit": UNIT, "ms": ms_batched,
+                              "updates": updates},
+            "per_volume": {"value": loop, "unit": UNIT, "ms": ms_loop,
+                           "updates": loop_updates},
+            "batched_over_per_volume": batched / loop}
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample_rate(raw, seconds_cap=30.0):
     """Updates/s of the FP64 oracle: IFCM iterations of one particle
@@ -270,7 +337,7 @@ def run_ours(args):
     vol = vol_host.to(dev)
     n_p, n_gen, n_it, n_init = P, GENERATIONS, MAX_ITER, INIT_MAX_ITER
     if args.small:       # short case for profiler captures: same volume and kernels
-        n_p, n_gen, n_it, n_init = 4, 1, 3, 3
+        n_p, n_gen, n_it, n_init = P, 1, 3, 3
     prm = G.Params(c=C, m=M, max_iter=n_it, eps_u=EPS)
     opts = G.Options(P=n_p, generations=n_gen, seed=rank_seed(rank), init_max_iter=n_init)
     bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
@@ -373,6 +440,8 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(vol_host.numel() * 4),
                     "d2h_bytes_per_step": int(u_host.numel() * 4 + 120)},
             "gpu_launches": args.steps * launches_per_run(INIT_MAX_ITER, GENERATIONS, MAX_ITER)}
+    if rank == 0 and not args.skip_batching:
+        line["batching"] = batching_leg(G, phantoms, dev)
     if plain is not None:
         line["plain"] = plain
         line["plain"]["batched_over_plain"] = value / world / plain["value"]
@@ -395,8 +464,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batching", action="store_true",
+                    help="leave out the uneven multi-volume batch")
     ap.add_argument("--small", action="store_true",
-                    help="profiling case: 4 particles x 1 generation x 3 iterations")
+                    help="profiling case: the same volume and particles, 1 generation x "
+                         "3 iterations")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

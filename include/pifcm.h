@@ -225,6 +225,10 @@ size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t 
 /* Smallest workspace that still runs (one volume per wave). */
 size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int32_t n,
                                              const ifcm_params* p);
+/* Waves (batched launch sequences) a call with ws_bytes of workspace runs;
+ * -1 on bad input or a workspace below the minimum. */
+int32_t pso_fitness_multi_waves(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
+                                size_t ws_bytes);
 ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
                               void* ws, size_t ws_bytes, void* stream);
 

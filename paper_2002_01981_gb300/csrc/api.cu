@@ -950,6 +950,18 @@ ifcm_status check_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_par
   return IFCM_OK;
 }
 
+// Volumes in the wave that starts at g[b]: as many as fit one launch
+// (kMaxVols volumes, kMaxBatchParticles particles) and ws_bytes.
+int wave_size(const ifcm_batch_volume* vols, const std::vector<int>& g, size_t b, int c,
+              size_t ws_bytes) {
+  int cnt = 0, parts = 0;
+  while (b + cnt < g.size() && cnt < kMaxVols &&
+         parts + vols[g[b + cnt]].P <= kMaxBatchParticles &&
+         wave_bytes(vols, g.data() + b, cnt + 1, c) <= ws_bytes)
+    parts += vols[g[b + cnt++]].P;
+  return cnt;
+}
+
 // Volumes of cluster count c, in input order.
 std::vector<int> group_of(const ifcm_batch_volume* vols, int n, int c) {
   std::vector<int> g;
@@ -970,10 +982,7 @@ size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t 
     const std::vector<int> g = group_of(vols, n, c);
     // whole group, in launch-sized pieces
     for (size_t b = 0; b < g.size();) {
-      int cnt = 0, parts = 0;
-      while (b + cnt < g.size() && cnt < kMaxVols &&
-             parts + vols[g[b + cnt]].P <= kMaxBatchParticles)
-        parts += vols[g[b + cnt++]].P;
+      const int cnt = wave_size(vols, g, b, c, static_cast<size_t>(-1));
       const size_t w = wave_bytes(vols, g.data() + b, cnt, c);
       if (w > need) need = w;
       b += cnt;
@@ -991,6 +1000,18 @@ size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int3
     if (w > need) need = w;
   }
   return need;
+}
+
+int32_t pso_fitness_multi_waves(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
+                                size_t ws_bytes) {
+  if (check_multi(vols, n, p) != IFCM_OK) return -1;
+  if (ws_bytes < pso_fitness_multi_min_workspace_bytes(vols, n, p)) return -1;
+  int32_t waves = 0;
+  for (int c = 2; c <= kMaxC; ++c) {
+    const std::vector<int> g = group_of(vols, n, c);
+    for (size_t b = 0; b < g.size(); ++waves) b += wave_size(vols, g, b, c, ws_bytes);
+  }
+  return waves;
 }
 
 ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_params* p,
@@ -1013,12 +1034,7 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
     ifcm_params pc = *p;
     pc.c = c;
     for (size_t b = 0; b < g.size();) {
-      // the next wave: as many volumes as fit the launch limits and ws_bytes
-      int cnt = 0, parts = 0;
-      while (b + cnt < g.size() && cnt < kMaxVols &&
-             parts + vols[g[b + cnt]].P <= kMaxBatchParticles &&
-             wave_bytes(vols, g.data() + b, cnt + 1, c) <= ws_bytes)
-        parts += vols[g[b + cnt++]].P;
+      const int cnt = wave_size(vols, g, b, c, ws_bytes);
       std::vector<BatchVol> bv(cnt);
       ifcm_shape shapes[kMaxVols];
       int P[kMaxVols];

@@ -277,6 +277,13 @@ def pso_fitness_multi_workspace_bytes(volumes, params, minimum=False):
     return fn(descs, len(volumes), ctypes.byref(p))
 
 
+def pso_fitness_multi_waves(volumes, params, ws_bytes):
+    lib = N.load()
+    descs, _keep, _ = _multi_descriptors(volumes)
+    p = params.native()
+    return lib.pso_fitness_multi_waves(descs, len(volumes), ctypes.byref(p), int(ws_bytes))
+
+
 def pso_fitness_multi(volumes, params, ws=None):
     """Fitness of every particle of every volume (volumes of the same c share
     each batched launch); ``params.c`` is ignored, each volume has its own.

@@ -73,6 +73,8 @@ SIGNATURES = {
                                                      POINTER(IfcmParams)]),
     "pso_fitness_multi_min_workspace_bytes": (c_size_t, [POINTER(IfcmBatchVolume), c_int32,
                                                          POINTER(IfcmParams)]),
+    "pso_fitness_multi_waves": (c_int32, [POINTER(IfcmBatchVolume), c_int32,
+                                          POINTER(IfcmParams), c_size_t]),
     "pso_fitness_multi": (c_int32, [POINTER(IfcmBatchVolume), c_int32, POINTER(IfcmParams),
                                     c_void_p, c_size_t, c_void_p]),
     "ifcm_autotune_enable": (None, [c_int32]),

@@ -223,3 +223,18 @@ def test_stencil_plan_rule_and_forcing(lib):
     assert lib.ifcm_stencil_force_plan(0, 0) == 0
     lib.ifcm_stencil_plan(N.IfcmShape(64, 64, 1, 64), 4, 1, ctypes.byref(npp), ctypes.byref(tz))
     assert tz.value == 1
+
+
+def test_multi_volume_wave_count(lib):
+    p = _params()
+    a = ((40, 32, 24, 40), 3, 6)
+    b = ((24, 24, 24, 24), 3, 5)
+    d = ((16, 16, 16, 16), 5, 1)
+    vols = _batch_volumes([a, d, b])
+    full = lib.pso_fitness_multi_workspace_bytes(vols, 3, ctypes.byref(p))
+    lo = lib.pso_fitness_multi_min_workspace_bytes(vols, 3, ctypes.byref(p))
+    assert lib.pso_fitness_multi_waves(vols, 3, ctypes.byref(p), full) == 2      # one per c
+    assert lib.pso_fitness_multi_waves(vols, 3, ctypes.byref(p), lo) == 3        # one per volume
+    assert lib.pso_fitness_multi_waves(vols, 3, ctypes.byref(p), lo - 256) == -1
+    many = _batch_volumes([((8, 8, 8, 8), 3, 1)] * 70)
+    assert lib.pso_fitness_multi_waves(many, 70, ctypes.byref(p), 1 << 40) == 2   # 64 + 6
