@@ -257,6 +257,95 @@ def batching_leg(G, phantoms, dev):
             "batched_over_per_volume": batched / loop}
 
 
+# ------------------------------------------- membership storage precision
+PREC_SHAPE = (256, 256, 256)
+PREC_C, PREC_P = 6, 64
+PREC_WORKLOAD = ("background + 5 tissues 256^3 (0/0.2/0.35/0.5/0.7/0.9), Rician sigma 0.1, c=6, "
+                 "m=2, 26-neighbourhood, one generation of 64 particles (swarm init, seed 5), "
+                 f"<= {MAX_ITER} IFCM iterations per fitness, stop max|du|<{EPS:g}")
+
+
+def precision_leg(G, phantoms, dev):
+    """One generation's fitness batch of the c = 6 workload with FP32
+    memberships, bf16 memberships (FP64 sums) and bf16 memberships with
+    compensated FP32 sums: updates/s, the stencil kernel's achieved bytes,
+    and the bf16 forms' agreement with the FP32 form at full size (fitness,
+    iteration counts; labels, centres and J of one run at the FP32 form's
+    best particle).  Errors against the FP64 oracle are measured by the GPU
+    tests on a slab of this workload."""
+    import torch
+    raw = phantoms.multi_tissue(PREC_SHAPE, seed=5, sigma=0.1)
+    nz, ny, nx = PREC_SHAPE
+    N = nz * ny * nx
+    vol = torch.from_numpy(phantoms.pad_pitch(raw)).to(dev)
+    del raw
+    x = G.ifcm_normalize(vol, nx=nx)
+    del vol
+    U0, C0, _, it0 = G.ifcm_fit(x, G.Params(c=PREC_C, m=M, max_iter=INIT_MAX_ITER, eps_u=EPS),
+                                (0.0, 0.0), nx=nx)
+    sw = G.Swarm(PREC_P, seed=5).init()
+    lam_xi = sw.x.clone()
+    variants = [("fp32", "fp64"), ("bf16", "fp64"), ("bf16", "comp32")]
+    need = max(G.pso_fitness_batch_workspace_bytes(
+        x, G.Params(c=PREC_C, u_dtype=d, reduce=r), PREC_P, nx=nx) for d, r in variants)
+    ws = G.workspace(need, dev)
+    hbm, _ = peaks()
+    out = {"workload": PREC_WORKLOAD, "fcm_start_iterations": int(it0), "variants": {}}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    fits = {}
+    for d, r in variants:
+        prm = G.Params(c=PREC_C, m=M, max_iter=MAX_ITER, eps_u=EPS, u_dtype=d, reduce=r)
+        G.pso_fitness_batch(x, prm, lam_xi, U0, C0, nx=nx, ws=ws)        # warm
+        torch.cuda.synchronize()
+        G.profile_read()
+        G.profile_enable(True)
+        ev0.record()
+        fit, its, _ = G.pso_fitness_batch(x, prm, lam_xi, U0, C0, nx=nx, ws=ws)
+        ev1.record()
+        torch.cuda.synchronize()
+        G.profile_enable(False)
+        kms, nl = G.profile_read()
+        ms = ev0.elapsed_time(ev1)
+        upd = int(its.sum()) * N
+        np_, _, _ = G.stencil_plan(G.shape_of(x, nx), PREC_C, PREC_P)
+        s_u = 4 if d == "fp32" else 2
+        bpu = 2 * PREC_C * s_u + 4.0 / np_
+        ach = upd * bpu / (kms / 1e3) / 1e9
+        fits[(d, r)] = (fit.cpu().numpy(), its.cpu().numpy())
+        out["variants"][f"{d}/{r}"] = {
+            "value": upd / (ms / 1e3), "unit": UNIT, "ms": ms, "updates": upd,
+            "stencil": {"bytes_per_update": bpu, "achieved_gbs": ach, "frac": ach / hbm,
+                        "kernel_ms": kms, "launches": nl}}
+    f32, i32 = fits[("fp32", "fp64")]
+    best = int(np.argmin(f32))
+    lx = lam_xi[best].cpu().numpy()
+    prm32 = G.Params(c=PREC_C, m=M, max_iter=MAX_ITER, eps_u=EPS)
+    U32, C32, J32, _ = G.ifcm_fit(x, prm32, lx, nx=nx, u_init=U0, c_init=C0)
+    lab32 = torch.argmax(U32[..., :nx], dim=0)
+    c32 = C32.cpu().numpy()
+    del U32
+    for d, r in variants[1:]:
+        fb, ib = fits[(d, r)]
+        prm = G.Params(c=PREC_C, m=M, max_iter=MAX_ITER, eps_u=EPS, u_dtype=d, reduce=r)
+        Ub, Cb, Jb, _ = G.ifcm_fit(x, prm, lx, nx=nx, u_init=U0, c_init=C0)
+        agree = float((torch.argmax(Ub[..., :nx], dim=0) == lab32).double().mean())
+        del Ub
+        out["variants"][f"{d}/{r}"]["vs_fp32"] = {
+            "fitness_max_rel": float(np.max(np.abs(fb / f32 - 1.0))),
+            "iterations_equal": float(np.mean(ib == i32)),
+            "best_particle_run": {"labels_agree": agree,
+                                  "centres_max_rel": float(np.max(np.abs(Cb.cpu().numpy() / c32
+                                                                         - 1.0))),
+                                  "J_rel": abs(Jb / J32 - 1.0)}}
+    v32 = out["variants"]["fp32/fp64"]["value"]
+    for k, v in out["variants"].items():
+        v["over_fp32"] = v["value"] / v32
+    del ws, x, U0
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample_rate(raw, seconds_cap=30.0):
     """Updates/s of the FP64 oracle: IFCM iterations of one particle
@@ -442,6 +531,8 @@ def run_ours(args):
             "gpu_launches": args.steps * launches_per_run(INIT_MAX_ITER, GENERATIONS, MAX_ITER)}
     if rank == 0 and not args.skip_batching:
         line["batching"] = batching_leg(G, phantoms, dev)
+    if rank == 0 and not args.skip_precision:
+        line["precision"] = precision_leg(G, phantoms, dev)
     if plain is not None:
         line["plain"] = plain
         line["plain"]["batched_over_plain"] = value / world / plain["value"]
@@ -466,6 +557,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batching", action="store_true",
                     help="leave out the uneven multi-volume batch")
+    ap.add_argument("--skip-precision", action="store_true",
+                    help="leave out the FP32 / bf16 membership storage comparison")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same volume and particles, 1 generation x "
                          "3 iterations")

@@ -68,7 +68,25 @@ typedef struct {
   int32_t max_iter;          /* IFCM iterations per run, >= 1                     */
   double eps_u;              /* stop when max_ij |u' - u| < eps_u                 */
   double dist_floor;         /* lower bound of d^2 (reading R2), e.g. 1e-12       */
+  int32_t u_dtype;           /* IFCM_U_FP32 (0) or IFCM_U_BF16 (1): see below     */
+  int32_t reduce;            /* IFCM_REDUCE_FP64 (0) or IFCM_REDUCE_COMP32 (1)    */
 } ifcm_params;
+
+/* Storage of the memberships between the iterations of the batched runs
+ * (ifcm_fit, pso_fitness_batch, pso_fitness_multi*, pifcm3d).  The paper
+ * fixes no precision.  IFCM_U_BF16 stores U^t as bfloat16 (rounded to nearest
+ * even once per iteration) while every arithmetic step stays FP32; it halves
+ * the membership traffic.  max|du| of the stop rule compares the stored
+ * values.  Inputs (u_init, u0) and outputs (u_out) stay FP32 arrays either
+ * way.  The plain form (ifcm_fit_plain) and the FCM start always use FP32. */
+#define IFCM_U_FP32 0
+#define IFCM_U_BF16 1
+/* Precision of the centre / objective sums above the warp level (Eqs 1, 3):
+ * IFCM_REDUCE_FP64 sums warp partials and tile records in FP64;
+ * IFCM_REDUCE_COMP32 sums them in FP32 with Neumaier compensation and takes
+ * Eq 3 in FP32.  Within a thread and a warp the sums are FP32 either way. */
+#define IFCM_REDUCE_FP64 0
+#define IFCM_REDUCE_COMP32 1
 
 /* Swarm state (Algorithm 1 steps 3-8).  All arrays are device memory owned by
  * the caller: x, v, pbest_x hold P*2 doubles (lambda, xi per particle),

@@ -16,6 +16,8 @@ Modules
                    SC'11) and the 53-bit uniform double built from it.
 ``oracle.pso``     Algorithm 1 steps 3-9 (particle swarm over (lambda, xi))
                    and the whole Algorithm 1 driver.
+``oracle.precision``  bfloat16 rounding (nearest, ties to even) from the
+                   format's definition, to model membership storage.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, hand-worked fixtures under

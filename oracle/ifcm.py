@@ -185,12 +185,16 @@ def centres(x, U, m):
 # --------------------------------------------------------------------------
 # The step function and its loop (Alg 1 step 4 / Alg 2 steps 6-10)
 # --------------------------------------------------------------------------
-def ifcm_iteration(x, U, C, lam, xi, m=2.0, V=1, h=1.0, dist_floor=1e-12):
+def ifcm_iteration(x, U, C, lam, xi, m=2.0, V=1, h=1.0, dist_floor=1e-12, store=None):
     """One IFCM iteration t: (U^t, C^t) -> (U^{t+1}, C^{t+1}, J^t, delta^t).
 
     H and F come from U^t (R6); d^2 from C^t (Eq 4); U^{t+1} from Eq 2;
     J^t from Eq 1 with that d^2 (R7); C^{t+1} from Eq 3;
     delta^t = max_ij |u^{t+1}_ij - u^t_ij|.
+
+    ``store`` (optional) models a storage format for the memberships: the
+    returned U^{t+1} is store(U^{t+1}), and delta compares stored values.
+    J^t and C^{t+1} are still taken from the unrounded U^{t+1}.
     """
     if lam == 0.0 and xi == 0.0:
         H = F = 0.0                       # Eq 4 reduces to plain FCM
@@ -200,24 +204,29 @@ def ifcm_iteration(x, U, C, lam, xi, m=2.0, V=1, h=1.0, dist_floor=1e-12):
     U1 = membership(d2, m)
     J = objective(U1, d2, m)
     C1 = centres(x, U1, m)
+    if store is not None:
+        U1 = store(U1)
     delta = float(np.max(np.abs(U1 - U)))
     return U1, C1, J, delta
 
 
 def ifcm_fit(x, U0, C0, lam, xi, m=2.0, max_iter=50, eps=1e-5, V=1, h=1.0,
-             dist_floor=1e-12, history=False):
+             dist_floor=1e-12, history=False, store=None):
     """Run IFCM from (U0, C0) until delta < eps or max_iter iterations (R5).
 
     Returns (U, C, J_last, iterations) and, with ``history``, the list of
-    (J^t, delta^t) per iteration.
+    (J^t, delta^t) per iteration.  ``store`` models the storage format of the
+    memberships (see ``ifcm_iteration``); the start U0 is stored first.
     """
     U = np.asarray(U0, dtype=np.float64)
+    if store is not None:
+        U = store(U)
     C = np.asarray(C0, dtype=np.float64)
     J = float("nan")
     hist = []
     it = 0
     for it in range(1, max_iter + 1):
-        U, C, J, delta = ifcm_iteration(x, U, C, lam, xi, m, V, h, dist_floor)
+        U, C, J, delta = ifcm_iteration(x, U, C, lam, xi, m, V, h, dist_floor, store)
         hist.append((J, delta))
         if delta < eps:
             break

@@ -64,8 +64,15 @@ ifcm_status check_params(const ifcm_params* p) {
   if (!(p->eps_u >= 0.0)) return fail(IFCM_ERR_INVALID, "eps_u = %g must be >= 0", p->eps_u);
   if (!(p->dist_floor > 0.0) || !(p->dist_floor < 1.0))
     return fail(IFCM_ERR_INVALID, "dist_floor = %g must lie in (0, 1)", p->dist_floor);
+  if (p->u_dtype != IFCM_U_FP32 && p->u_dtype != IFCM_U_BF16)
+    return fail(IFCM_ERR_INVALID, "u_dtype = %d: expected IFCM_U_FP32 or IFCM_U_BF16", p->u_dtype);
+  if (p->reduce != IFCM_REDUCE_FP64 && p->reduce != IFCM_REDUCE_COMP32)
+    return fail(IFCM_ERR_INVALID, "reduce = %d: expected IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32",
+                p->reduce);
   return IFCM_OK;
 }
+
+bool is_bf16(const ifcm_params* p) { return p->u_dtype == IFCM_U_BF16; }
 
 // The kernels index one particle's c membership planes with 32-bit offsets.
 ifcm_status check_extent(const ifcm_shape& s, const ifcm_params* p) {
@@ -133,10 +140,16 @@ constexpr int kPlainVpt = 32;
 // buffers per volume (P particles each), the partial records of every
 // particle's tiles, and the per-particle run state (particle p of volume v is
 // state index pbase[v] + p).
+// With bf16 memberships ua / ub hold pair words for either plan (np = 1 or
+// 2, whichever is larger) and u0p the packed shared start; np is the plan
+// the last run used (it fixes the word layout).
 struct RunBufs {
   int n;
+  bool bf16;
+  int np;
   float* ua[kMaxVols];
   float* ub[kMaxVols];
+  float* u0p[kMaxVols];
   int pbase[kMaxVols];
   long long rec_base[kMaxVols];
   int rec_per_particle[kMaxVols];
@@ -145,15 +158,28 @@ struct RunBufs {
   RunState st;
 };
 
-RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, int c) {
+// 4-byte elements per voxel of one membership buffer of P particles.
+size_t run_buffer_elems(int c, int P, bool bf16) {
+  if (!bf16) return static_cast<size_t>(P) * c;
+  long long w = bf16_unit_words(c, 1, P);
+  if (c <= 4 && bf16_unit_words(c, 2, P) > w) w = bf16_unit_words(c, 2, P);
+  // the FCM start (FP32, one particle) also runs in these buffers
+  if (w < c) w = c;
+  return static_cast<size_t>(w);
+}
+
+RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, int c,
+                   bool bf16) {
   RunBufs r{};
   r.n = n;
+  r.bf16 = bf16;
   long long recs = 0;
   int pb = 0;
   for (int v = 0; v < n; ++v) {
     const size_t pl = plane_elems(shapes[v]);
-    r.ua[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
-    r.ub[v] = cv.take<float>(static_cast<size_t>(P[v]) * c * pl);
+    r.ua[v] = cv.take<float>(run_buffer_elems(c, P[v], bf16) * pl);
+    r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], bf16) * pl);
+    r.u0p[v] = bf16 ? cv.take<float>(static_cast<size_t>(c) * pl) : nullptr;
     const long long nvox = static_cast<long long>(shapes[v].nx) * shapes[v].ny * shapes[v].nz;
     int nrec = max_tiles(shapes[v]);
     const int nplain = plain_blocks(nvox, kPlainVpt);      // the plain kernel's records (P = 1)
@@ -174,8 +200,8 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
   return r;
 }
 
-RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P) {
-  return carve_runs(cv, &s, &P, 1, c);
+RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P, bool bf16) {
+  return carve_runs(cv, &s, &P, 1, c, bf16);
 }
 
 RunState shifted(const RunState& st, int pbase, int c) {
@@ -296,6 +322,7 @@ void fill_method(StencilArgs& a, const ifcm_params* p) {
   a.m = static_cast<float>(p->m);
   a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
   a.m_is_2 = p->m == 2.0;
+  a.reduce = p->reduce;
 }
 
 // One volume of a batch of IFCM runs (host view).
@@ -328,8 +355,8 @@ long long plan_items(const BatchVol* vols, int n, const StencilPlan& pl) {
   return items;
 }
 
-int plan_grid(int c, const StencilPlan& pl, long long items) {
-  long long g = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np);
+int plan_grid(int c, bool bf16, const StencilPlan& pl, long long items) {
+  long long g = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np, bf16);
   if (g > items) g = items;
   return g < 1 ? 1 : static_cast<int>(g);
 }
@@ -344,9 +371,9 @@ int most_chunks(const BatchVol* vols, int n) {
 // Built-in choice: the deepest chunks that still give every CTA of the
 // persistent grid at least four items (whole columns when the batch is big
 // enough: fewer halo planes and pipeline fills per voxel).
-StencilPlan heuristic_plan(const BatchVol* vols, int n, int c) {
+StencilPlan heuristic_plan(const BatchVol* vols, int n, int c, bool bf16) {
   StencilPlan pl{stencil_default_np(c), 1};
-  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np);
+  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np, bf16);
   const int kmax = most_chunks(vols, n);
   while (pl.chunks < kmax && plan_items(vols, n, pl) < want) ++pl.chunks;
   return pl;
@@ -359,10 +386,10 @@ struct Tuner {
   std::map<std::vector<long long>, StencilPlan> cache;
 } g_tune;
 
-// Cache key: element type of the memberships (0 = FP32), c, and every
-// volume's extent and particle count.
-std::vector<long long> plan_key(const BatchVol* vols, int n, int c) {
-  std::vector<long long> k{0, c, n};
+// Cache key: element type of the memberships (an IFCM_U_* value), c, and
+// every volume's extent and particle count.
+std::vector<long long> plan_key(const BatchVol* vols, int n, int c, int u_dtype) {
+  std::vector<long long> k{u_dtype, c, n};
   for (int v = 0; v < n; ++v) {
     const ifcm_shape& s = vols[v].shape;
     k.insert(k.end(), {s.nx, s.ny, s.nz, vols[v].P});
@@ -401,14 +428,36 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.pbase = rb.pbase[v];
     d.rec_base = rb.rec_base[v];
     d.lam_xi = bv.lam_xi;
-    const float* src = kind == 0 ? bv.u0 : (kind == 1 ? rb.ua[v] : rb.ub[v]);
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
-    d.u_src = src;
-    d.src_pstride = kind == 0 ? 0 : static_cast<long long>(c) * plane;
-    d.src_cstride = kind == 0 ? 0 : c;
     ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
-    ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? c : bv.P * c, c));
+    if (rb.bf16) {
+      // pair words: K planes per unit (a particle pair for np = 2, a particle
+      // for np = 1); iteration 0 reads the packed shared start (one unit)
+      const int K = pl.np == 2 ? c : (c + 1) / 2;
+      const int units = pl.np == 2 ? (bv.P + 1) / 2 : bv.P;
+      const float* src = kind == 0 ? rb.u0p[v] : (kind == 1 ? rb.ua[v] : rb.ub[v]);
+      d.u_src = src;
+      d.src_pstride = kind == 0 ? 0 : static_cast<long long>(K) * plane;
+      d.src_cstride = kind == 0 ? 0 : K;
+      ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? K : units * K, K));
+    } else {
+      const float* src = kind == 0 ? bv.u0 : (kind == 1 ? rb.ua[v] : rb.ub[v]);
+      d.u_src = src;
+      d.src_pstride = kind == 0 ? 0 : static_cast<long long>(c) * plane;
+      d.src_cstride = kind == 0 ? 0 : c;
+      ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? c : bv.P * c, c));
+    }
   }
+  return IFCM_OK;
+}
+
+// bf16 runs: each volume's shared start as pair words laid out for np.
+ifcm_status pack_starts(const BatchVol* vols, int n, int c, const RunBufs& rb, int np,
+                        cudaStream_t st) {
+  if (!rb.bf16) return IFCM_OK;
+  for (int v = 0; v < n; ++v)
+    CU_TRY(launch_pack_start(vols[v].u0, reinterpret_cast<uint32_t*>(rb.u0p[v]), c, np,
+                             static_cast<long long>(plane_elems(vols[v].shape)), st));
   return IFCM_OK;
 }
 
@@ -419,7 +468,8 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
 ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
                       DevStatus* status, cudaStream_t st, StencilPlan* best) {
   const int c = p->c;
-  const StencilPlan h = heuristic_plan(vols, n, c);
+  const bool bf = is_bf16(p);
+  const StencilPlan h = heuristic_plan(vols, n, c, bf);
   const int kmax = most_chunks(vols, n);
   std::vector<StencilPlan> cand;
   for (int np = 1; np <= 2; ++np) {
@@ -443,10 +493,13 @@ ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const R
     rc = build_args(args[0], vols, n, p, rb, pl, 0, status);
     if (rc == IFCM_OK) rc = build_args(args[1], vols, n, p, rb, pl, 1, status);
     if (rc != IFCM_OK) break;
-    const int grid = plan_grid(c, pl, plan_items(vols, n, pl));
-    cudaError_t e = launch_stencil(c, pl.np, args[0], grid, st);
+    const int grid = plan_grid(c, bf, pl, plan_items(vols, n, pl));
+    rc = pack_starts(vols, n, c, rb, pl.np, st);
+    if (rc != IFCM_OK) break;
+    cudaError_t e = launch_stencil(c, pl.np, bf, args[0], grid, st);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_stencil(c, pl.np, args[1], grid, st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+      e = launch_stencil(c, pl.np, bf, args[1], grid, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -467,7 +520,7 @@ ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const R
 
 ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
                         DevStatus* status, cudaStream_t st, StencilPlan* out) {
-  const std::vector<long long> key = plan_key(vols, n, p->c);
+  const std::vector<long long> key = plan_key(vols, n, p->c, p->u_dtype);
   int mode;
   {
     std::lock_guard<std::mutex> lk(g_tune.mu);
@@ -485,7 +538,7 @@ ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU_TRY(cudaStreamIsCapturing(st, &cap));
   if (mode == 0 || cap != cudaStreamCaptureStatusNone) {
-    *out = heuristic_plan(vols, n, p->c);      // a stream being captured is never timed
+    *out = heuristic_plan(vols, n, p->c, is_bf16(p));   // a captured stream is never timed
     return IFCM_OK;
   }
   ST_TRY(tune_plan(vols, n, p, rb, status, st, out));
@@ -507,6 +560,9 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
   }
   StencilPlan pl;
   ST_TRY(choose_plan(vols, n, p, rb, status, st, &pl));
+  const bool bf = rb.bf16;
+  rb.np = pl.np;
+  ST_TRY(pack_starts(vols, n, c, rb, pl.np, st));
   // Three parameter blocks: iteration 0 (U0 -> ua), odd (ua -> ub), even (ub -> ua).
   std::vector<StencilArgs> args(3);
   for (int k = 0; k < 3; ++k) ST_TRY(build_args(args[k], vols, n, p, rb, pl, k, status));
@@ -518,6 +574,7 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
   r.st = rb.st;
   r.max_iter = p->max_iter;
   r.eps = p->eps_u;
+  r.reduce = p->reduce;
   r.status = status;
   for (int v = 0; v < n; ++v) {
     ReduceVol& rv = r.vol[v];
@@ -530,12 +587,12 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
     rv.iters_out = vols[v].iters;
     rv.c_out = vols[v].c_out;
   }
-  const int grid = plan_grid(c, pl, plan_items(vols, n, pl));
+  const int grid = plan_grid(c, bf, pl, plan_items(vols, n, pl));
   for (int it = 0; it < p->max_iter; ++it) {
     const StencilArgs& a = args[it == 0 ? 0 : (it % 2 == 1 ? 1 : 2)];
     cudaEvent_t ev_end = nullptr;
     cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-    CU_TRY(launch_stencil(c, pl.np, a, grid, st));
+    CU_TRY(launch_stencil(c, pl.np, bf, a, grid, st));
     if (ev_beg) cudaEventRecord(ev_end, st);
     CU_TRY(launch_reduce(c, r, st));
   }
@@ -549,6 +606,18 @@ ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* 
                         DevStatus* status, cudaStream_t st) {
   BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out};
   return run_stencil_batch(&bv, 1, p, rb, status, st);
+}
+
+// Particle 0's final memberships (P = 1 runs) as FP32 [c][plane].
+ifcm_status copy_out(const RunBufs& rb, int c, size_t plane, float* u_out, cudaStream_t st) {
+  if (rb.bf16)
+    CU_TRY(launch_unpack_select(reinterpret_cast<const uint32_t*>(rb.ua[0]),
+                                reinterpret_cast<const uint32_t*>(rb.ub[0]), rb.st.iters, u_out,
+                                c, rb.np, static_cast<long long>(plane), st));
+  else
+    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out,
+                              static_cast<long long>(c) * plane, st));
+  return IFCM_OK;
 }
 
 // One run with the plain kernel (P = 1).  host_check: read max|du| after
@@ -670,7 +739,7 @@ PifcmBufs carve_pifcm(Carver& cv, const ifcm_shape& s, const ifcm_params* p,
   b.J_init = cv.take<double>(1);
   b.updates = cv.take<unsigned long long>(1);
   b.norm = carve_norm(cv, s);
-  b.run = carve_run(cv, rs, c, P);
+  b.run = carve_run(cv, rs, c, P, is_bf16(p));
   return b;
 }
 
@@ -763,7 +832,7 @@ size_t ifcm_fit_workspace_bytes(ifcm_shape shape, const ifcm_params* p) {
   Carver cv(nullptr);
   carve_status(cv);
   cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));   // uniform start
-  carve_run(cv, shape, p->c, 1);
+  carve_run(cv, shape, p->c, 1, is_bf16(p));
   return cv.off + 256;
 }
 
@@ -785,7 +854,7 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
   float* uni = cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
-  RunBufs rb = carve_run(cv, shape, p->c, 1);
+  RunBufs rb = carve_run(cv, shape, p->c, 1, is_bf16(p));
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   const float* start = u_init;
@@ -795,9 +864,7 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
   }
   ST_TRY(run_stencil(x, shape, p, lam_xi, 1, start, c_init, rb, J_out, iters_out, c_out, status,
                      st));
-  if (u_out)
-    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out,
-                              static_cast<long long>(p->c) * plane_elems(shape), st));
+  if (u_out) ST_TRY(copy_out(rb, p->c, plane_elems(shape), u_out, st));
   return IFCM_OK;
 }
 
@@ -807,6 +874,8 @@ ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* 
                            size_t ws_bytes, void* stream) {
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
+  if (p->u_dtype != IFCM_U_FP32)
+    return fail(IFCM_ERR_UNSUPPORTED, "the plain form stores FP32 memberships only");
   ST_TRY(check_extent(shape, p));
   ST_TRY(check_aligned(x, "x"));
   ST_TRY(check_aligned(ws, "ws"));
@@ -817,7 +886,7 @@ ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* 
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
   cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
-  RunBufs rb = carve_run(cv, shape, p->c, 1);
+  RunBufs rb = carve_run(cv, shape, p->c, 1, false);
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   ST_TRY(run_plain(x, shape, p, nullptr, static_cast<float>(lambda), static_cast<float>(xi),
@@ -834,7 +903,7 @@ size_t pso_fitness_batch_workspace_bytes(ifcm_shape shape, const ifcm_params* p,
   if (!p || p->c < 2 || p->c > kMaxC || P < 1) return 0;
   Carver cv(nullptr);
   carve_status(cv);
-  carve_run(cv, shape, p->c, P);
+  carve_run(cv, shape, p->c, P, is_bf16(p));
   return cv.off + 256;
 }
 
@@ -856,7 +925,7 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
-  RunBufs rb = carve_run(cv, shape, p->c, P);
+  RunBufs rb = carve_run(cv, shape, p->c, P, is_bf16(p));
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   return run_stencil(x, shape, p, lam_xi, P, u0, c0, rb, fitness, iters, c_out, status, st);
@@ -895,11 +964,11 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
   BatchVol bv{};
   bv.shape = shape;
   bv.P = P;
-  StencilPlan pl = heuristic_plan(&bv, 1, c);
+  StencilPlan pl = heuristic_plan(&bv, 1, c, false);
   int32_t tuned = 0;
   {
     std::lock_guard<std::mutex> lk(g_tune.mu);
-    auto it = g_tune.cache.find(plan_key(&bv, 1, c));
+    auto it = g_tune.cache.find(plan_key(&bv, 1, c, IFCM_U_FP32));
     if (g_tune.force.np > 0 && stencil_np_supported(c, g_tune.force.np)) {
       pl = g_tune.force;
     } else if (it != g_tune.cache.end()) {
@@ -917,7 +986,7 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
 // -------------------------------------------------- pso_fitness_multi
 namespace {
 
-size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c) {
+size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c, bool bf16) {
   ifcm_shape shapes[kMaxVols];
   int P[kMaxVols];
   for (int i = 0; i < n; ++i) {
@@ -926,7 +995,7 @@ size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c) {
   }
   Carver cv(nullptr);
   carve_status(cv);
-  carve_runs(cv, shapes, P, n, c);
+  carve_runs(cv, shapes, P, n, c, bf16);
   return cv.off + 256;
 }
 
@@ -953,11 +1022,11 @@ ifcm_status check_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_par
 // Volumes in the wave that starts at g[b]: as many as fit one launch
 // (kMaxVols volumes, kMaxBatchParticles particles) and ws_bytes.
 int wave_size(const ifcm_batch_volume* vols, const std::vector<int>& g, size_t b, int c,
-              size_t ws_bytes) {
+              bool bf16, size_t ws_bytes) {
   int cnt = 0, parts = 0;
   while (b + cnt < g.size() && cnt < kMaxVols &&
          parts + vols[g[b + cnt]].P <= kMaxBatchParticles &&
-         wave_bytes(vols, g.data() + b, cnt + 1, c) <= ws_bytes)
+         wave_bytes(vols, g.data() + b, cnt + 1, c, bf16) <= ws_bytes)
     parts += vols[g[b + cnt++]].P;
   return cnt;
 }
@@ -982,8 +1051,8 @@ size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t 
     const std::vector<int> g = group_of(vols, n, c);
     // whole group, in launch-sized pieces
     for (size_t b = 0; b < g.size();) {
-      const int cnt = wave_size(vols, g, b, c, static_cast<size_t>(-1));
-      const size_t w = wave_bytes(vols, g.data() + b, cnt, c);
+      const int cnt = wave_size(vols, g, b, c, is_bf16(p), static_cast<size_t>(-1));
+      const size_t w = wave_bytes(vols, g.data() + b, cnt, c, is_bf16(p));
       if (w > need) need = w;
       b += cnt;
     }
@@ -996,7 +1065,7 @@ size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int3
   if (check_multi(vols, n, p) != IFCM_OK) return 0;
   size_t need = 0;
   for (int i = 0; i < n; ++i) {
-    const size_t w = wave_bytes(vols, &i, 1, vols[i].c);
+    const size_t w = wave_bytes(vols, &i, 1, vols[i].c, is_bf16(p));
     if (w > need) need = w;
   }
   return need;
@@ -1009,7 +1078,7 @@ int32_t pso_fitness_multi_waves(const ifcm_batch_volume* vols, int32_t n, const 
   int32_t waves = 0;
   for (int c = 2; c <= kMaxC; ++c) {
     const std::vector<int> g = group_of(vols, n, c);
-    for (size_t b = 0; b < g.size(); ++waves) b += wave_size(vols, g, b, c, ws_bytes);
+    for (size_t b = 0; b < g.size(); ++waves) b += wave_size(vols, g, b, c, is_bf16(p), ws_bytes);
   }
   return waves;
 }
@@ -1034,7 +1103,7 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
     ifcm_params pc = *p;
     pc.c = c;
     for (size_t b = 0; b < g.size();) {
-      const int cnt = wave_size(vols, g, b, c, ws_bytes);
+      const int cnt = wave_size(vols, g, b, c, is_bf16(p), ws_bytes);
       std::vector<BatchVol> bv(cnt);
       ifcm_shape shapes[kMaxVols];
       int P[kMaxVols];
@@ -1046,7 +1115,7 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
       }
       Carver cv(ws);
       DevStatus* status = carve_status(cv);
-      RunBufs rb = carve_runs(cv, shapes, P, cnt, c);
+      RunBufs rb = carve_runs(cv, shapes, P, cnt, c, is_bf16(p));
       CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
       ST_TRY(run_stencil_batch(bv.data(), cnt, &pc, rb, status, st));
       b += cnt;
@@ -1199,9 +1268,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));
   ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
                      b.c_final, b.status, st));
-  if (u_out)
-    CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out, static_cast<long long>(c) * rpl,
-                              st));
+  if (u_out) ST_TRY(copy_out(rb, c, rpl, u_out, st));
   CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
                        b.iters_init, b.updates, b.best, b.status, result, st));
   return IFCM_OK;

@@ -4,6 +4,8 @@
 // run's final memberships, and the result block.
 #include <math_constants.h>
 
+#include <cuda_bf16.h>
+
 #include "launch.h"
 
 namespace pifcm {
@@ -96,6 +98,48 @@ __global__ void select_copy_kernel(const float4* a, const float4* b, const int32
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n4;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
     dst[i] = src[i];
+}
+
+// ------------------------------------------------ bf16 pair-word buffers
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);   // lo in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Shared start as pair words: np = 2 -> word plane j = (u_j, u_j) (both
+// particles of every pair start from it); np = 1 -> word plane k =
+// (u_2k, u_2k+1), with 0 in the high half past the last cluster.
+__global__ void pack_start_kernel(const float* u0, uint32_t* out, int c, int np,
+                                  long long plane) {
+  const int planes = np == 2 ? c : (c + 1) / 2;
+  const long long n = static_cast<long long>(planes) * plane;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long k = i / plane, v = i - k * plane;
+    if (np == 2) {
+      const float u = u0[k * plane + v];
+      out[i] = bf16_pair(u, u);
+    } else {
+      const float lo = u0[(2 * k) * plane + v];
+      const float hi = 2 * k + 1 < c ? u0[(2 * k + 1) * plane + v] : 0.0f;
+      out[i] = bf16_pair(lo, hi);
+    }
+  }
+}
+
+// Particle 0's memberships (unit 0, low lane for np = 2) as FP32 planes.
+__global__ void unpack_select_kernel(const uint32_t* a, const uint32_t* b,
+                                     const int32_t* iters, float* dst, int c, int np,
+                                     long long plane) {
+  const uint32_t* src = ((*iters) & 1) ? a : b;
+  const long long n = static_cast<long long>(c) * plane;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long j = i / plane, v = i - j * plane;
+    const uint32_t w = np == 2 ? src[j * plane + v] : src[(j >> 1) * plane + v];
+    const bool hi = np == 2 ? false : (j & 1);
+    dst[i] = __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+  }
 }
 
 __global__ void fill_kernel(float* dst, float value, long long n) {
@@ -255,6 +299,26 @@ cudaError_t launch_select_copy(const float* a, const float* b, const int32_t* it
   select_copy_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
       reinterpret_cast<const float4*>(a), reinterpret_cast<const float4*>(b), iters,
       reinterpret_cast<float4*>(dst), n4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_start(const float* u0, uint32_t* out, int c, int np, long long plane,
+                              cudaStream_t s) {
+  const long long n = static_cast<long long>(np == 2 ? c : (c + 1) / 2) * plane;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  pack_start_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(u0, out, c, np, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_select(const uint32_t* a, const uint32_t* b, const int32_t* iters,
+                                 float* dst, int c, int np, long long plane, cudaStream_t s) {
+  const long long n = static_cast<long long>(c) * plane;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  unpack_select_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(a, b, iters, dst, c, np, plane);
   return cudaGetLastError();
 }
 

@@ -165,4 +165,50 @@ __device__ __noinline__ void flat_neighbourhood_mean(const float* __restrict__ u
   for (int j = 0; j < C; ++j) H[j] = s[j] * inv;
 }
 
+// The same mean over bf16 pair words (two memberships per 32-bit word, low
+// half first): with pair_particles, word plane j holds cluster j of a particle
+// pair and `lane` picks the particle; otherwise word plane j/2 holds clusters
+// 2(j/2) and 2(j/2)+1 of one particle.
+template <int C>
+__device__ __noinline__ void flat_neighbourhood_mean_bf16(const uint32_t* __restrict__ u,
+                                                          bool pair_particles, int lane, int X,
+                                                          int Y, int Z, int nx, int ny, int nz,
+                                                          int pitch, float (&H)[C]) {
+  const size_t plane = static_cast<size_t>(nz) * ny * pitch;
+  float s[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) s[j] = 0.0f;
+  int n = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+        if (kx < 0 || kx >= nx || ky < 0 || ky >= ny || kz < 0 || kz >= nz) continue;
+        const size_t off = (static_cast<size_t>(kz) * ny + ky) * pitch + kx;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const int wp = pair_particles ? j : j >> 1;
+          const int hi = pair_particles ? lane : (j & 1);
+          const uint32_t w = u[wp * plane + off];
+          s[j] += __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+        }
+        ++n;
+      }
+  const float inv = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) H[j] = s[j] * inv;
+}
+
+// Compensated (Neumaier) FP32 summation step: sum + comp carries the running
+// total with the rounding error of every addition kept in comp.
+__device__ __forceinline__ void neumaier_add(float& sum, float& comp, float v) {
+  const float t = __fadd_rn(sum, v);
+  if (fabsf(sum) >= fabsf(v))
+    comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, t), v));
+  else
+    comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(v, t), sum));
+  sum = t;
+}
+
 }  // namespace pifcm

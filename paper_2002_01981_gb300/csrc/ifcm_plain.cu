@@ -139,6 +139,68 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
 // centres, the Eq 1 objective, and the stop rule of the run.
 constexpr int RT = 256;
 
+// Per-particle finalisation with compensated FP32 sums instead of FP64: each
+// thread sums its records with Neumaier's method, the (sum, compensation)
+// pairs are combined pairwise in shared memory, and Eqs 3 and 1 are taken in
+// FP32 from sum + compensation.  max|du| and the stop rule are as in FP64.
+// s_hi, s_lo: NV x RT floats each; s_mx: RT floats (the FP64 path's shared
+// arrays, reused).
+template <int C>
+__device__ __noinline__ void reduce_comp32(const ReduceArgs& a, const ReduceVol& rv, int gp,
+                                           int p, const double* rec, long long first,
+                                           float (*s_hi)[RT], float (*s_lo)[RT], float* s_mx) {
+  constexpr int NV = 2 * C + 1;
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) hi[v] = lo[v] = 0.0f;
+  float mx = 0.0f;
+  for (int r = threadIdx.x; r < rv.n_rec; r += RT) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      neumaier_add(hi[v], lo[v], static_cast<float>(rec[static_cast<size_t>(r) * NV + v]));
+    mx = fmaxf(mx, a.dmax[first + r]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    s_hi[v][threadIdx.x] = hi[v];
+    s_lo[v][threadIdx.x] = lo[v];
+  }
+  s_mx[threadIdx.x] = mx;
+  __syncthreads();
+  for (int h = RT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float sh = s_hi[v][threadIdx.x], sl = s_lo[v][threadIdx.x];
+        neumaier_add(sh, sl, s_hi[v][threadIdx.x + h]);
+        s_hi[v][threadIdx.x] = sh;
+        s_lo[v][threadIdx.x] = __fadd_rn(sl, s_lo[v][threadIdx.x + h]);
+      }
+      s_mx[threadIdx.x] = fmaxf(s_mx[threadIdx.x], s_mx[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* cen = a.st.centres + static_cast<size_t>(gp) * C;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const float S0 = __fadd_rn(s_hi[j][0], s_lo[j][0]);
+      const float S1 = __fadd_rn(s_hi[C + j][0], s_lo[C + j][0]);
+      if (S0 > 0.0f) cen[j] = static_cast<double>(__fdiv_rn(S1, S0));   // Eq 3
+      if (rv.c_out) rv.c_out[static_cast<size_t>(p) * C + j] = cen[j];
+    }
+    const double J = static_cast<double>(__fadd_rn(s_hi[2 * C][0], s_lo[2 * C][0]));  // Eq 1
+    a.st.J[gp] = J;
+    const int it = a.st.iters[gp] + 1;
+    a.st.iters[gp] = it;
+    if (rv.fitness) rv.fitness[p] = J;
+    if (rv.iters_out) rv.iters_out[p] = it;
+    const double delta = static_cast<double>(s_mx[0]);
+    if (!(delta >= a.eps) || it >= a.max_iter) a.st.active[gp] = 0;
+    atomicAdd(a.st.updates, static_cast<unsigned long long>(rv.nvox));
+  }
+}
+
 template <int C>
 __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
   constexpr int NV = 2 * C + 1;
@@ -156,6 +218,11 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
   float mx = 0.0f;
   const long long first = rv.rec_base + static_cast<long long>(p) * rv.n_rec;
   const double* rec = a.partials + first * NV;
+  if (a.reduce == IFCM_REDUCE_COMP32) {
+    float(*fs)[RT] = reinterpret_cast<float(*)[RT]>(&s_sum[0][0]);
+    reduce_comp32<C>(a, rv, gp, p, rec, first, fs, fs + NV, s_max);
+    return;
+  }
   for (int r = threadIdx.x; r < rv.n_rec; r += RT) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] += rec[static_cast<size_t>(r) * NV + v];

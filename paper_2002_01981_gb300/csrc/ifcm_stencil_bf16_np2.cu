@@ -1,0 +1,33 @@
+// The stencil kernel over bf16 pair words with two particles per work item
+// (c <= 4): word (pair k, cluster j) holds cluster j of particles 2k and
+// 2k+1, the two lanes of the packed FP32x2 sums.
+#include "stencil_kernel.cuh"
+
+namespace pifcm {
+
+size_t smem_bytes_bf16_np2(int c) {
+  switch (c) {
+    case 2: return smem_total<2, 2, true>();
+    case 3: return smem_total<3, 2, true>();
+    default: return smem_total<4, 2, true>();
+  }
+}
+
+int blocks_per_sm_bf16_np2(int c) {
+  switch (c) {
+    case 2: return blocks_per_sm_c<2, 2, true>();
+    case 3: return blocks_per_sm_c<3, 2, true>();
+    default: return blocks_per_sm_c<4, 2, true>();
+  }
+}
+
+cudaError_t launch_stencil_bf16_np2(int c, const StencilArgs& a, int grid, cudaStream_t s) {
+  switch (c) {
+    case 2: return launch_c<2, 2, true>(a, grid, s);
+    case 3: return launch_c<3, 2, true>(a, grid, s);
+    case 4: return launch_c<4, 2, true>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pifcm

@@ -52,16 +52,22 @@ struct StencilArgs {
   float* dmax;                  // [records]
   float dist_floor, m, inv_m1;
   int m_is_2;
+  int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across warps
   DevStatus* status;
 };
 static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
 
 // np = particles sharing one work item: 1 for every c, 2 for c <= 4.
+// bf16: memberships stored as bf16 pair words (see stencil_kernel.cuh).
 bool stencil_np_supported(int c, int np);
 int stencil_default_np(int c);
-size_t stencil_smem_bytes(int c, int np);
-int stencil_blocks_per_sm(int c, int np);
-cudaError_t launch_stencil(int c, int np, const StencilArgs& a, int grid, cudaStream_t s);
+size_t stencil_smem_bytes(int c, int np, bool bf16);
+int stencil_blocks_per_sm(int c, int np, bool bf16);
+cudaError_t launch_stencil(int c, int np, bool bf16, const StencilArgs& a, int grid,
+                           cudaStream_t s);
+// 32-bit words per voxel of one pair-word membership buffer of P particles
+// laid out for np: ceil(P/2) * c (np = 2) or P * ceil(c/2) (np = 1).
+long long bf16_unit_words(int c, int np, int P);
 
 // ------------------------------------- plain iteration (one thread per voxel)
 struct PlainArgs {
@@ -105,6 +111,7 @@ struct ReduceArgs {
   RunState st;                  // arrays over the launch's particles
   int max_iter;
   double eps;
+  int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across records
   DevStatus* status;
   ReduceVol vol[kMaxVols];
 };
@@ -122,6 +129,14 @@ cudaError_t launch_scale(const float* v, float* x, int nx, int ny, int nz, int p
 cudaError_t launch_fill(float* dst, float value, long long n, cudaStream_t s);
 cudaError_t launch_select_copy(const float* a, const float* b, const int32_t* iters,
                                float* dst, long long n, cudaStream_t s);
+// Pair words of a shared start: u0 [c][plane] FP32 -> [c][plane] words (u, u)
+// for np = 2, or [ceil(c/2)][plane] words (u_2k, u_2k+1) for np = 1.
+cudaError_t launch_pack_start(const float* u0, uint32_t* out, int c, int np, long long plane,
+                              cudaStream_t s);
+// Particle 0's memberships from the pair-word buffer its last iteration wrote
+// (a after an odd number of iterations, else b) as FP32 [c][plane].
+cudaError_t launch_unpack_select(const uint32_t* a, const uint32_t* b, const int32_t* iters,
+                                 float* dst, int c, int np, long long plane, cudaStream_t s);
 cudaError_t launch_pso_init(const pso_state& st, cudaStream_t s);
 cudaError_t launch_pso_step(const pso_state& st, const double* fitness, cudaStream_t s);
 cudaError_t launch_pso_best(const double* pbest_x, const double* pbest_f, int P,

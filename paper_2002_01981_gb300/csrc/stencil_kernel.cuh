@@ -29,7 +29,20 @@
 // sum_k g_ik.  Per item and particle, the sums go to a partial record (FP32
 // within a thread and a warp, FP64 across warps) that the reduce kernel sums
 // per particle in FP64.
+//
+// BF16 memberships (BF = true): U^t and U^{t+1} are stored as bf16 pairs, one
+// 32-bit word per (voxel, pair): the two particles of a fixed pair (2k, 2k+1)
+// for the same cluster when NP = 2, or clusters (2k, 2k+1) of one particle
+// when NP = 1 -- the same pairing as the packed FP32x2 sums, low half first.
+// The TMA tiles therefore still move 4-byte elements (a pair plane has the
+// shape of an FP32 plane), one shared-memory load yields a whole pair, and
+// one 32-bit store writes one.  All arithmetic stays FP32: a word is unpacked
+// exactly (bf16 -> f32 is a shift) and u' is rounded to nearest even once,
+// when it is stored.  max|du| compares the stored (rounded) values; the sums of
+// Eqs 1 and 3 use the FP32 u' that the rounding was applied to.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "ifcm_math.cuh"
 #include "launch.h"
@@ -68,20 +81,37 @@ template <int C>
 __host__ __device__ constexpr int ufloats() {
   return ubytes<C>() / 4;
 }
+// Pairs per voxel: with two particles per item, pair k is cluster k of both;
+// with one, pair k is clusters 2k and 2k+1.
 template <int C, int NP>
+struct Pairs {
+  static constexpr int K = NP == 2 ? C : (C + 1) / 2;
+};
+// 32-bit membership planes of one stage: c per particle in FP32, one per pair
+// in BF16.
+template <int C, int NP, bool BF>
+__host__ __device__ constexpr int uplanes() {
+  return BF ? Pairs<C, NP>::K : NP * C;
+}
+// Bytes of a stage's membership block (every TMA destination 128-B aligned).
+template <int C, int NP, bool BF>
+__host__ __device__ constexpr int ublock_bytes() {
+  return BF ? ((Pairs<C, NP>::K * PLANE * 4 + 127) / 128) * 128 : NP * ubytes<C>();
+}
+template <int C, int NP, bool BF>
 __host__ __device__ constexpr int stage_bytes() {
-  return XBYTES + NP * ubytes<C>();
+  return XBYTES + ublock_bytes<C, NP, BF>();
 }
 static_assert(XBYTES % 128 == 0 && ubytes<3>() % 128 == 0 && ubytes<5>() % 128 == 0 &&
                   ubytes<7>() % 128 == 0,
               "TMA shared-memory destinations must start on 128-byte boundaries");
-template <int C, int NP>
+template <int C, int NP, bool BF>
 __host__ __device__ constexpr uint32_t stage_tx_bytes() {
-  return static_cast<uint32_t>((1 + NP * C) * PLANE * 4);
+  return static_cast<uint32_t>((1 + uplanes<C, NP, BF>()) * PLANE * 4);
 }
-template <int C, int NP>
+template <int C, int NP, bool BF>
 __host__ __device__ constexpr int smem_total() {
-  return NSTAGE * stage_bytes<C, NP>() + 128;
+  return NSTAGE * stage_bytes<C, NP, BF>() + 128;
 }
 
 __device__ __forceinline__ void consumer_sync() {
@@ -102,19 +132,29 @@ __device__ __forceinline__ float gdist(float a, float b) {
 struct Item {
   int v;               // volume
   int p0, p1;          // the volume's particles of the group (p1 = p0 when the group has one)
-  bool two;            // p1 is a distinct particle
+  bool on0;            // p0 is running (its partial record is written)
+  bool two;            // p1 is a distinct, running particle
+  int unit;            // BF16: the pair (NP = 2) or particle (NP = 1) whose words are loaded
   int tile, x0, y0, z0, z1, pzb, pze;
 };
 
-// Work items of a launch, numbered volume by volume: the active particles of
-// volume v (s_act[vfirst[v] ...], vnact[v] of them) in groups of NP, times the
-// volume's tiles; vitem[v] is the volume's first item.
+// Work items of a launch, numbered volume by volume: the active units of
+// volume v (act[vfirst[v] ...], vnact[v] of them) in groups, times the
+// volume's tiles; vitem[v] is the volume's first item.  A unit is a particle,
+// grouped NP at a time; with BF16 pairs of particles (NP = 2) it is a fixed
+// pair (2k, 2k+1), active while either runs, one per group.
 struct ItemTable {
   short act[kMaxBatchParticles];
   int vfirst[kMaxVols], vnact[kMaxVols], vitem[kMaxVols + 1];
 };
 
-template <int NP>
+// Units of a group: NP particles in FP32, one unit (pair or particle) in BF16.
+template <int NP, bool BF>
+__host__ __device__ constexpr int group_units() {
+  return BF ? 1 : NP;
+}
+
+template <int NP, bool BF>
 __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTable& tab, int w) {
   Item it;
   int v = 0;
@@ -125,9 +165,21 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTabl
   const int g = wl / vd.n_tiles;
   it.tile = wl - g * vd.n_tiles;
   const short* act = tab.act + tab.vfirst[v];
-  it.p0 = act[g * NP];
-  it.two = (NP == 2) && (g * NP + 1 < tab.vnact[v]);
-  it.p1 = it.two ? act[g * NP + 1] : it.p0;
+  if (BF && NP == 2) {
+    const int u = act[g];
+    const bool has1 = 2 * u + 1 < vd.P;
+    it.unit = u;
+    it.p0 = 2 * u;
+    it.p1 = has1 ? 2 * u + 1 : 2 * u;
+    it.on0 = a.active[vd.pbase + it.p0] != 0;
+    it.two = has1 && a.active[vd.pbase + it.p1] != 0;
+  } else {
+    it.p0 = act[g * NP];
+    it.on0 = true;
+    it.two = (NP == 2) && (g * NP + 1 < tab.vnact[v]);
+    it.p1 = it.two ? act[g * NP + 1] : it.p0;
+    it.unit = it.p0;
+  }
   const int per_z = vd.tiles_x * vd.tiles_y;
   const int zc = it.tile / per_z;
   const int rem = it.tile - zc * per_z;
@@ -147,13 +199,21 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTabl
 // item, pair k holds cluster k of particle 0 and of particle 1; with one, pair
 // k holds clusters 2k and 2k+1 (the second half of the last pair is unused
 // when c is odd).
-template <int C, int NP>
-struct Pairs {
-  static constexpr int K = NP == 2 ? C : (C + 1) / 2;
-};
 
-template <int C, int NP>
+// A bf16 pair word as two exact floats (low half first).
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+// Two floats rounded to nearest even into one bf16 pair word (x in the low half).
+__device__ __forceinline__ uint32_t pack_bf16x2(float2 v) {
+  const __nv_bfloat162 h = __float22bfloat162_rn(v);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int C, int NP, bool BF>
 __device__ __forceinline__ float2 load_pair(const float* __restrict__ us, int k, int off) {
+  if (BF) return unpack_bf16x2(reinterpret_cast<const uint32_t*>(us)[k * PLANE + off]);
   if (NP == 2) return make_float2(us[k * PLANE + off], us[ufloats<C>() + k * PLANE + off]);
   const float lo = us[(2 * k) * PLANE + off];
   const float hi = (2 * k + 1 < C) ? us[(2 * k + 1) * PLANE + off] : 0.0f;
@@ -211,7 +271,7 @@ struct ItemConst {
 // the plane's window sums A = sum w and B = sum (dx^2 + dy^2) w (w = u^2): the
 // planes above and below weigh q^2 = 1 + dx^2 + dy^2 (A + B), the same plane
 // dx^2 + dy^2 (B).
-template <int C, int NP, bool Z3>
+template <int C, int NP, bool BF, bool Z3>
 __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
                                                  const float* __restrict__ us, int cidx,
                                                  float x_lo, float x_mid, float x_hi,
@@ -243,7 +303,7 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
       const float2 gl2 = dup2(gl), gh2 = dup2(gh), gm2 = dup2(gm);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float2 uk = load_pair<C, NP>(us, k, off);
+        const float2 uk = load_pair<C, NP, BF>(us, k, off);
         if (Z3) {
           lo.H[k] = __ffma2_rn(uk, gl2, lo.H[k]);
           hi.H[k] = __ffma2_rn(uk, gh2, hi.H[k]);
@@ -281,7 +341,7 @@ __device__ __forceinline__ float2 max2(float2 v, float lo) {
 // Finalise one centre (its u^t is read from its plane's stage at cus): H and F
 // (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
 // the centre's shares of Eqs 1 and 3, in packed pairs.
-template <int C, int NP>
+template <int C, int NP, bool BF>
 __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
                                                 int cidx, float xc, int z, bool interior,
                                                 const VolDesc& a, const Item& it,
@@ -318,8 +378,14 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       for (int p = 0; p < NP; ++p) {
         const int pid = p == 0 ? it.p0 : it.p1;
         float Hm[C];
-        flat_neighbourhood_mean<C>(a.u_src + static_cast<long long>(pid) * a.src_pstride, cx.X,
-                                   cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
+        if (BF)
+          flat_neighbourhood_mean_bf16<C>(
+              reinterpret_cast<const uint32_t*>(a.u_src) +
+                  static_cast<long long>(it.unit) * a.src_pstride,
+              NP == 2, p, cx.X, cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
+        else
+          flat_neighbourhood_mean<C>(a.u_src + static_cast<long long>(pid) * a.src_pstride,
+                                     cx.X, cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           if (NP == 2) {
@@ -413,6 +479,29 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
   const int plane = a.nz * a.ny * a.pitch;              // c * plane < 2^31 (host-checked)
   const int voff = z * (a.ny * a.pitch) + cx.col_off;
+  if (BF) {
+    // one rounded pair word per pair; max|du| between stored values
+    // (with one particle and an odd c, the high half of the last word is
+    // padding: stored as 0 and left out of max|du|)
+    uint32_t* dst = reinterpret_cast<uint32_t*>(ic.dst[0]);
+    const uint32_t* cw = reinterpret_cast<const uint32_t*>(cus);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const bool pad_hi = NP == 1 && 2 * q + 1 >= C;
+      const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
+      const uint32_t w = pack_bf16x2(uq);
+      dst[q * plane + voff] = w;
+      const float2 nr = unpack_bf16x2(w), old = unpack_bf16x2(cw[q * PLANE + cidx]);
+      const float e0 = fabsf(nr.x - old.x), e1 = fabsf(nr.y - old.y);
+      if (NP == 2) {
+        acc.dm[0] = fmaxf(acc.dm[0], e0);
+        acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
+      } else {
+        acc.dm[0] = fmaxf(acc.dm[0], pad_hi ? e0 : fmaxf(e0, e1));
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     if (p == 1 && !it.two) break;
@@ -425,7 +514,7 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
 }
 
-template <int C, int NP>
+template <int C, int NP, bool BF>
 __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     stencil_kernel(const __grid_constant__ StencilArgs a) {
   extern __shared__ unsigned char dsmem_raw[];
@@ -441,13 +530,20 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  // Active particles of every volume, compacted one volume per warp (ballots).
+  // Active units of every volume, compacted one volume per warp (ballots).
+  constexpr bool kPairUnits = BF && NP == 2;
   for (int v = warp; v < a.n_vol; v += NT / 32) {
     const VolDesc& vd = a.vol[v];
+    const int units = kPairUnits ? (vd.P + 1) / 2 : vd.P;
     int n = 0;
-    for (int base = 0; base < vd.P; base += 32) {
+    for (int base = 0; base < units; base += 32) {
       const int p = base + lane;
-      const bool on = p < vd.P && a.active[vd.pbase + p] != 0;
+      bool on;
+      if (kPairUnits)
+        on = p < units && (a.active[vd.pbase + 2 * p] != 0 ||
+                           (2 * p + 1 < vd.P && a.active[vd.pbase + 2 * p + 1] != 0));
+      else
+        on = p < units && a.active[vd.pbase + p] != 0;
       const unsigned m = __ballot_sync(0xffffffffu, on);
       if (on) tab.act[vd.pbase + n + __popc(m & ((1u << lane) - 1u))] = static_cast<short>(p);
       n += __popc(m);
@@ -470,7 +566,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     int items = 0;
     for (int v = 0; v < a.n_vol; ++v) {
       tab.vitem[v] = items;
-      items += ((tab.vnact[v] + NP - 1) / NP) * a.vol[v].n_tiles;
+      constexpr int GU = group_units<NP, BF>();
+      items += ((tab.vnact[v] + GU - 1) / GU) * a.vol[v].n_tiles;
     }
     tab.vitem[a.n_vol] = items;
   }
@@ -478,9 +575,11 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   const int n_items = tab.vitem[a.n_vol];
   if (static_cast<int>(blockIdx.x) >= n_items) return;
 
-  auto xs_of = [&](int s) { return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP>()); };
+  auto xs_of = [&](int s) {
+    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, BF>());
+  };
   auto us_of = [&](int s) {
-    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP>() + XBYTES);
+    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, BF>() + XBYTES);
   };
 
   // ------------------------------------------------------------ producer
@@ -488,7 +587,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     if (lane == 0) {
       int q = 0;
       for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const Item it = decode_item<NP>(a, tab, w);
+        const Item it = decode_item<NP, BF>(a, tab, w);
         const VolDesc& vd = a.vol[it.v];
         const CUtensorMap* mx = &a.tm_x[it.v];
         const CUtensorMap* mu = &a.tm_u[it.v];
@@ -501,11 +600,11 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
             return;
           }
           if (*reinterpret_cast<volatile int*>(&s_abort)) return;
-          mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP>());
+          mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP, BF>());
           tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
           tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                      it.p0 * vd.src_cstride);
-          if (NP == 2)
+                      (BF ? it.unit : it.p0) * vd.src_cstride);
+          if (NP == 2 && !BF)
             tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
                         it.p1 * vd.src_cstride);
         }
@@ -541,7 +640,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   };
 
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const Item it = decode_item<NP>(a, tab, w);
+    const Item it = decode_item<NP, BF>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
     const bool z3 = vd.nz > 1;
     const int plane = vd.nz * vd.ny * vd.pitch;
@@ -561,7 +660,9 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
 #pragma unroll
         for (int j = 0; j < C; ++j)
           cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
-        if (p < NP) s_ic.dst[p] = vd.u_dst + static_cast<size_t>(pid) * C * plane;
+        if (p < NP)
+          s_ic.dst[p] = BF ? vd.u_dst + static_cast<size_t>(it.unit) * Pairs<C, NP>::K * plane
+                           : vd.u_dst + static_cast<size_t>(pid) * C * plane;
       }
       s_ic.nlam = make_float2(-lam[0], -lam[1]);
       s_ic.nxi = make_float2(-xi[0], -xi[1]);
@@ -600,14 +701,14 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         const int zd = pz - 2;
         if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
           const int sdi = (qq + NSTAGE - 2) % NSTAGE;
-          finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
+          finalize_centre<C, NP, BF>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
                                  cx.col_interior && zd > 0 && zd < vd.nz - 1, vd, it, s_ic, cx,
                                  k, acc);
         }
         if (z3)
-          accumulate_plane<C, NP, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          accumulate_plane<C, NP, BF, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
         else
-          accumulate_plane<C, NP, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          accumulate_plane<C, NP, BF, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
       }
       if (kk >= 2) release(qq - 2);
       sd = sl;
@@ -622,13 +723,13 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
       if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
         const int sdi = (ql + NSTAGE - 1) % NSTAGE;
-        finalize_centre<C, NP>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
+        finalize_centre<C, NP, BF>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
                                cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
                                it, s_ic, cx, k, acc);
       }
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
         const int sli = ql % NSTAGE;
-        finalize_centre<C, NP>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
+        finalize_centre<C, NP, BF>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
                                cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
       }
       if (np >= 2) release(ql - 1);
@@ -658,14 +759,21 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     consumer_sync();
     if (tid < NP * (2 * C + 2)) {
       const int p = tid / (2 * C + 2), v = tid - p * (2 * C + 2);
-      if (p == 0 || it.two) {
+      if (p == 0 ? it.on0 : it.two) {
         const int pid = p == 0 ? it.p0 : it.p1;
         const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
         if (v < 2 * C + 1) {
-          double sum = 0.0;
+          if (a.reduce == IFCM_REDUCE_FP64) {
+            double sum = 0.0;
 #pragma unroll
-          for (int wv = 0; wv < NCW; ++wv) sum += static_cast<double>(s_red[wv][tid]);
-          a.partials[rec * (2 * C + 1) + v] = sum;
+            for (int wv = 0; wv < NCW; ++wv) sum += static_cast<double>(s_red[wv][tid]);
+            a.partials[rec * (2 * C + 1) + v] = sum;
+          } else {   // compensated FP32 (Neumaier) across the warps
+            float sum = 0.0f, comp = 0.0f;
+#pragma unroll
+            for (int wv = 0; wv < NCW; ++wv) neumaier_add(sum, comp, s_red[wv][tid]);
+            a.partials[rec * (2 * C + 1) + v] = static_cast<double>(__fadd_rn(sum, comp));
+          }
         } else {
           float mm = 0.0f;
 #pragma unroll
@@ -678,23 +786,23 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   }
 }
 // ---------------------------------------------------------------------------
-template <int C, int NP>
+template <int C, int NP, bool BF>
 cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
-  constexpr int smem = smem_total<C, NP>();
-  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP>,
+  constexpr int smem = smem_total<C, NP, BF>();
+  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, BF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil_kernel<C, NP><<<grid, NT, smem, s>>>(a);
+  stencil_kernel<C, NP, BF><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int C, int NP>
+template <int C, int NP, bool BF>
 int blocks_per_sm_c() {
   int n = 0;
-  constexpr int smem = smem_total<C, NP>();
-  cudaFuncSetAttribute(stencil_kernel<C, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int smem = smem_total<C, NP, BF>();
+  cudaFuncSetAttribute(stencil_kernel<C, NP, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP>, NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP, BF>, NT, smem) !=
       cudaSuccess)
     return 1;
   return n > 0 ? n : 1;

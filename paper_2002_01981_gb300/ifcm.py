@@ -43,10 +43,17 @@ def shape_of(vol, nx=None):
     return N.IfcmShape(int(nx if nx is not None else pitch), int(ny), int(nz), int(pitch))
 
 
+_U_DTYPES = {"fp32": N.IFCM_U_FP32, "bf16": N.IFCM_U_BF16}
+_REDUCES = {"fp64": N.IFCM_REDUCE_FP64, "comp32": N.IFCM_REDUCE_COMP32}
+
+
 @dataclass
 class Params:
     """Method parameters (Algorithm 1 inputs): clusters c, fuzzifier m, the
-    iteration cap and stop threshold of one IFCM run, the d^2 floor."""
+    iteration cap and stop threshold of one IFCM run, the d^2 floor; and the
+    storage of the memberships between iterations ("fp32" or "bf16") and the
+    precision of the centre / objective sums above the warp ("fp64" or
+    "comp32", compensated FP32)."""
     c: int = 4
     m: float = 2.0
     max_iter: int = 50
@@ -54,10 +61,16 @@ class Params:
     dist_floor: float = 1e-12
     V: int = 1
     h: float = 1.0
+    u_dtype: str = "fp32"
+    reduce: str = "fp64"
 
     def native(self):
+        if self.u_dtype not in _U_DTYPES:
+            raise ValueError(f"u_dtype must be one of {sorted(_U_DTYPES)}")
+        if self.reduce not in _REDUCES:
+            raise ValueError(f"reduce must be one of {sorted(_REDUCES)}")
         return N.IfcmParams(self.c, self.m, self.V, self.h, self.max_iter, self.eps_u,
-                            self.dist_floor)
+                            self.dist_floor, _U_DTYPES[self.u_dtype], _REDUCES[self.reduce])
 
 
 @dataclass
@@ -141,6 +154,12 @@ def ifcm_fit(x, params, lam_xi, nx=None, u_init=None, c_init=None, ws=None, plai
 
 
 # ---------------------------------------------- Alg 1 step 4, whole swarm
+def pso_fitness_batch_workspace_bytes(x, params, P, nx=None):
+    """Workspace bytes of a ``pso_fitness_batch`` call with P particles."""
+    p = params.native()
+    return N.load().pso_fitness_batch_workspace_bytes(shape_of(x, nx), ctypes.byref(p), int(P))
+
+
 def pso_fitness_batch(x, params, lam_xi, u0, c0, nx=None, ws=None, want_centres=False):
     """Fitness (J of an IFCM run from (u0, c0)) of every particle; returns
     (fitness [P] float64, iterations [P] int32, centres [P, c] or None)."""

@@ -21,9 +21,14 @@ class IfcmShape(Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("pitch_x", c_int32)]
 
 
+IFCM_U_FP32, IFCM_U_BF16 = 0, 1
+IFCM_REDUCE_FP64, IFCM_REDUCE_COMP32 = 0, 1
+
+
 class IfcmParams(Structure):
     _fields_ = [("c", c_int32), ("m", c_double), ("V", c_int32), ("h", c_double),
-                ("max_iter", c_int32), ("eps_u", c_double), ("dist_floor", c_double)]
+                ("max_iter", c_int32), ("eps_u", c_double), ("dist_floor", c_double),
+                ("u_dtype", c_int32), ("reduce", c_int32)]
 
 
 class PsoState(Structure):

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_the_header_layout():
     from paper_2002_01981_gb300 import native as N
     assert ctypes.sizeof(N.IfcmShape) == 16
-    assert ctypes.sizeof(N.IfcmParams) == 56
+    assert ctypes.sizeof(N.IfcmParams) == 64
     assert ctypes.sizeof(N.PsoState) == 64
     assert ctypes.sizeof(N.PifcmOptions) == 40
     assert ctypes.sizeof(N.PifcmResult) == 8 * 8 + 4 * 8 + 8 + 4 * 4
@@ -48,10 +48,11 @@ def test_struct_sizes_match_the_header_layout():
 
 def _params(**kw):
     from paper_2002_01981_gb300 import native as N
-    d = dict(c=4, m=2.0, V=1, h=1.0, max_iter=50, eps_u=1e-5, dist_floor=1e-12)
+    d = dict(c=4, m=2.0, V=1, h=1.0, max_iter=50, eps_u=1e-5, dist_floor=1e-12, u_dtype=0,
+             reduce=0)
     d.update(kw)
     return N.IfcmParams(d["c"], d["m"], d["V"], d["h"], d["max_iter"], d["eps_u"],
-                        d["dist_floor"])
+                        d["dist_floor"], d["u_dtype"], d["reduce"])
 
 
 @pytest.mark.parametrize("shape,ok", [((181, 217, 181, 184), True), ((5, 1, 1, 8), True),
@@ -73,7 +74,8 @@ def test_shape_validation(lib, shape, ok):
 @pytest.mark.parametrize("kw,status", [(dict(c=1), 1), (dict(c=9), 1), (dict(m=1.0), 1),
                                        (dict(m=float("nan")), 1), (dict(V=2), 6),
                                        (dict(max_iter=0), 1), (dict(eps_u=-1.0), 1),
-                                       (dict(dist_floor=0.0), 1)])
+                                       (dict(dist_floor=0.0), 1), (dict(u_dtype=2), 1),
+                                       (dict(u_dtype=-1), 1), (dict(reduce=2), 1)])
 def test_parameter_validation(lib, kw, status):
     from paper_2002_01981_gb300 import native as N
     shp = N.IfcmShape(8, 8, 8, 8)
