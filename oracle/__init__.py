@@ -18,6 +18,8 @@ Modules
                    and the whole Algorithm 1 driver.
 ``oracle.precision``  bfloat16 rounding (nearest, ties to even) from the
                    format's definition, to model membership storage.
+``oracle.adjoint`` reverse-mode dJ/d(lambda, xi) through K unrolled IFCM
+                   iterations (Eqs 1-8 differentiated by the chain rule).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, hand-worked fixtures under
