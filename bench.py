@@ -346,6 +346,113 @@ def precision_leg(G, phantoms, dev):
     return out
 
 
+# ---------------------------------------------------------- differentiation
+DIFF_SHAPE = (128, 128, 128)
+DIFF_C, DIFF_K, DIFF_P, DIFF_GEN, DIFF_STEPS = 4, 20, 20, 10, 10
+DIFF_WORKLOAD = ("nested ellipsoids 128^3 (0/0.25/0.55/0.85) + Gaussian sigma 0.09, c=4, m=2, "
+                 f"dJ/d(lambda, xi) through K={DIFF_K} unrolled IFCM iterations with per-iteration "
+                 f"membership checkpoints; swarm of {DIFF_P} x {DIFF_GEN} generations on the same "
+                 f"objective, then {DIFF_STEPS} projected gradient steps from its best particle")
+
+
+def differentiation_leg(G, phantoms, dev):
+    """Gradient evaluations of the c = 4 128^3 workload: time of one
+    ifcm_grad (checkpointed forward + reverse) with the adjoint kernels'
+    share and achieved bytes; a central-difference check of the gradient
+    on the FP32 forward (h = 1e-3); and the polish of the swarm's best
+    particle (J before / after)."""
+    import torch
+    raw = phantoms.gaussian_phantom(DIFF_SHAPE, seed=4, sigma=0.09)
+    nz, ny, nx = DIFF_SHAPE
+    N = nz * ny * nx
+    x = G.ifcm_normalize(torch.from_numpy(phantoms.pad_pitch(raw)).to(dev), nx=nx)
+    U0, C0, _, _ = G.ifcm_fit(x, G.Params(c=DIFF_C, m=M, max_iter=INIT_MAX_ITER, eps_u=EPS),
+                              (0.0, 0.0), nx=nx)
+    prm = G.Params(c=DIFF_C, m=M, max_iter=DIFF_K, eps_u=0.0)
+    sw = G.Swarm(DIFF_P, seed=4).init()
+    for _ in range(DIFF_GEN):
+        fit, _, _ = G.pso_fitness_batch(x, prm, sw.x, U0, C0, nx=nx)
+        sw.step(fit)
+    best = int(torch.argmin(sw.pbest_f))
+    start = sw.pbest_x[best].clone()
+    J0 = float(sw.pbest_f[best])
+    ws = G.workspace(G.ifcm_grad_workspace_bytes(x, prm, DIFF_K, nx=nx), dev)
+    G.ifcm_grad(x, prm, start, U0, C0, DIFF_K, nx=nx, ws=ws)              # warm
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for k in (G.PROF_STENCIL, G.PROF_ADJOINT_POINT, G.PROF_ADJOINT_GATHER):
+        G.profile_read(k)
+    G.profile_enable(True)
+    reps = 5
+    ev0.record()
+    for _ in range(reps):
+        J, g = G.ifcm_grad(x, prm, start, U0, C0, DIFF_K, nx=nx, ws=ws)
+    ev1.record()
+    torch.cuda.synchronize()
+    G.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / reps
+    fwd_ms, fwd_n = G.profile_read(G.PROF_STENCIL)
+    pt_ms, pt_n = G.profile_read(G.PROF_ADJOINT_POINT)
+    ga_ms, ga_n = G.profile_read(G.PROF_ADJOINT_GATHER)
+    g = g.cpu().numpy()
+    hbm, _ = peaks()
+    c = DIFF_C
+    # point kernel: x, U^t, u_bar^{t+1} (not at the last iteration) read, A, B, e
+    # written; gather: x, A, B, e, U^t read, u_bar^t written (4-byte elements)
+    pt_bytes = N * ((8 + 16 * c) * pt_n - 4 * c * reps) / pt_n
+    ga_bytes = N * (4 + 8 * c + 4 + 4 * c + 4 * c)
+    # the swarm's best sits where reading R8 drives it (large lambda + xi, the
+    # clamp of reading R2 active at many voxels); the derivative is checked
+    # and the polish shown at an interior point as well, where it is not
+    interior = np.array([0.3, 0.2])
+    h = 1e-3
+
+    def grad_check(pt):
+        J_, g_ = G.ifcm_grad(x, prm, pt, U0, C0, DIFF_K, nx=nx, ws=ws)
+        g_ = g_.cpu().numpy()
+        f = lambda a, b: float(G.ifcm_grad(x, prm, (a, b), U0, C0, DIFF_K, nx=nx, ws=ws)[0])  # noqa
+        fd = [(f(pt[0] + h, pt[1]) - f(pt[0] - h, pt[1])) / (2 * h),
+              (f(pt[0], pt[1] + h) - f(pt[0], pt[1] - h)) / (2 * h)]
+        return {"lambda_xi": [float(v) for v in pt], "J": float(J_), "grad": g_.tolist(),
+                "central_difference_h1e-3": fd,
+                "rel_diff": [abs(g_[i] / fd[i] - 1.0) if fd[i] else None for i in range(2)]}
+
+    def polish(pt):
+        J_start = float(G.ifcm_grad(x, prm, pt, U0, C0, DIFF_K, nx=nx, ws=ws)[0])
+        torch.cuda.synchronize()
+        ev0.record()
+        lp, Jp = G.ifcm_polish(x, prm, pt, U0, C0, DIFF_K, steps=DIFF_STEPS, step0=0.05,
+                               decay=0.7, nx=nx, ws=ws)
+        ev1.record()
+        torch.cuda.synchronize()
+        return {"steps": DIFF_STEPS, "ms": ev0.elapsed_time(ev1), "J_before": J_start,
+                "J_after": Jp, "lambda_xi_before": [float(v) for v in pt],
+                "lambda_xi_after": lp.cpu().numpy().tolist()}
+
+    lx = start.cpu().numpy()
+    out = {"workload": DIFF_WORKLOAD,
+           "grad_eval": {"ms": ms, "per_s": 1e3 / ms,
+                         "forward_stencil_ms": fwd_ms / reps,
+                         "adjoint_point": {"ms": pt_ms / reps,
+                                           "achieved_gbs": pt_bytes * pt_n / (pt_ms / 1e3) / 1e9,
+                                           "bytes_per_voxel": pt_bytes / N},
+                         "adjoint_gather": {"ms": ga_ms / reps,
+                                            "achieved_gbs": ga_bytes * ga_n / (ga_ms / 1e3) / 1e9,
+                                            "bytes_per_voxel": ga_bytes / N},
+                         "voxel_iterations_per_s": 2 * DIFF_K * N / (ms / 1e3)},
+           "swarm_best": {"lambda_xi": lx.tolist(), "pbest_J": J0,
+                          "grad": [float(v) for v in g]},
+           "interior_point": grad_check(interior),
+           "polish_from_swarm_best": polish(lx),
+           "polish_from_interior_point": polish(interior)}
+    for k in ("adjoint_point", "adjoint_gather"):
+        out["grad_eval"][k]["frac"] = out["grad_eval"][k]["achieved_gbs"] / hbm
+    del ws, x, U0
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample_rate(raw, seconds_cap=30.0):
     """Updates/s of the FP64 oracle: IFCM iterations of one particle
@@ -533,6 +640,8 @@ def run_ours(args):
         line["batching"] = batching_leg(G, phantoms, dev)
     if rank == 0 and not args.skip_precision:
         line["precision"] = precision_leg(G, phantoms, dev)
+    if rank == 0 and not args.skip_differentiation:
+        line["differentiation"] = differentiation_leg(G, phantoms, dev)
     if plain is not None:
         line["plain"] = plain
         line["plain"]["batched_over_plain"] = value / world / plain["value"]
@@ -559,6 +668,8 @@ def main():
                     help="leave out the uneven multi-volume batch")
     ap.add_argument("--skip-precision", action="store_true",
                     help="leave out the FP32 / bf16 membership storage comparison")
+    ap.add_argument("--skip-differentiation", action="store_true",
+                    help="leave out the gradient / polish leg")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same volume and particles, 1 generation x "
                          "3 iterations")

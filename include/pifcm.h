@@ -304,6 +304,41 @@ ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_par
                          void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Derivative of the fitness with respect to (lambda, xi) (Eqs 1-8 by the chain
+ * rule; the paper has no gradient).  The differentiated function is
+ * L(lambda, xi) = J^{K-1}: the objective of the last of K IFCM iterations from
+ * the fixed start (u0, c0), with no stop rule (the fitness of Algorithm 1 step
+ * 4 with eps_u = 0 and max_iter = K).  The forward pass keeps every U^t
+ * (checkpoints, K x c planes of the workspace) and a trace of C^{t+1},
+ * sum_i u^m and J^t.  The reverse pass runs back through Eq 3, Eq 1, Eq 2,
+ * Eq 4 (a clamp of reading R2 that is active passes no derivative) and the
+ * transposed neighbourhood stencils of Eqs 5 and 7.
+ * x: device, normalised volume.  lam_xi: device, 2 doubles.  u0: device
+ * [c][nz][ny][pitch_x].  c0: device, c doubles (both required).  J_out:
+ * device, 1 double (may be NULL).  grad_out: device, 2 doubles (dJ/dlambda,
+ * dJ/dxi).  p->eps_u and p->max_iter are ignored (K iterations).  FP32
+ * memberships only: IFCM_ERR_UNSUPPORTED for u_dtype = IFCM_U_BF16.
+ */
+size_t ifcm_grad_workspace_bytes(ifcm_shape shape, const ifcm_params* p, int32_t K);
+ifcm_status ifcm_grad(const float* x, ifcm_shape shape, const ifcm_params* p, int32_t K,
+                      const double* lam_xi, const float* u0, const double* c0, double* J_out,
+                      double* grad_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient polishing of a particle (e.g. the swarm's best): `steps` projected
+ * descent steps of fixed length on [0,1]^2,
+ *   (lambda, xi) <- clip((lambda, xi) - alpha_k g / |g|, 0, 1),
+ *   alpha_k = step0 * decay^k,
+ * with g = ifcm_grad at the current point.  Then J is evaluated at the last
+ * point.  lam_xi (device, 2 doubles) is read as the start and overwritten
+ * with the point of lowest J^{K-1} seen; J_out (device, 1 double, may be NULL)
+ * receives that J.  Workspace as for ifcm_grad.  Stream-ordered: no host
+ * synchronisation. */
+ifcm_status ifcm_polish(const float* x, ifcm_shape shape, const ifcm_params* p, int32_t K,
+                        int32_t steps, double step0, double decay, double* lam_xi,
+                        const float* u0, const double* c0, double* J_out, void* ws,
+                        size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * ifcm_fit without a caller workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * run a segmentation (a graph being recorded under global capture mode, a
@@ -333,6 +368,14 @@ ifcm_status ifcm_fit_noalloc(const float* x, ifcm_shape shape, const ifcm_params
  */
 void ifcm_profile_enable(int32_t on);
 ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches);
+/* The same for one kind of kernel: IFCM_PROF_STENCIL (what ifcm_profile_read
+ * returns), IFCM_PROF_ADJOINT_POINT or IFCM_PROF_ADJOINT_GATHER (the two
+ * kernels of each reverse iteration of ifcm_grad).  Reading a kind clears its
+ * records.  IFCM_ERR_INVALID for another kind. */
+#define IFCM_PROF_STENCIL 0
+#define IFCM_PROF_ADJOINT_POINT 1
+#define IFCM_PROF_ADJOINT_GATHER 2
+ifcm_status ifcm_profile_read_kind(int32_t kind, double* kernel_ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -290,13 +290,16 @@ int sm_count() {
 }
 
 // ------------------------------------------------------------ profiling
+// Event pairs around kernel launches of three kinds (IFCM_PROF_*): the
+// stencil iteration, the adjoint point kernel and the adjoint gather kernel.
 struct Profiler {
   std::mutex mu;
   bool on = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used, spare;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used[3];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
 } g_prof;
 
-cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out) {
+cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out, int kind = IFCM_PROF_STENCIL) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!g_prof.on) return nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -310,7 +313,7 @@ cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out) {
     cudaEventCreate(&ev.first);
     cudaEventCreate(&ev.second);
   }
-  g_prof.used.push_back(ev);
+  g_prof.used[kind].push_back(ev);
   cudaEventRecord(ev.first, s);
   *end_out = ev.second;
   return ev.first;
@@ -1323,10 +1326,12 @@ void ifcm_profile_enable(int32_t on) {
   g_prof.on = on != 0;
 }
 
-ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches) {
+ifcm_status ifcm_profile_read_kind(int32_t kind, double* kernel_ms, int64_t* launches) {
+  if (kind < 0 || kind > 2) return fail(IFCM_ERR_INVALID, "profile kind %d outside 0..2", kind);
   std::lock_guard<std::mutex> lk(g_prof.mu);
   double total = 0.0;
-  for (auto& ev : g_prof.used) {
+  auto& used = g_prof.used[kind];
+  for (auto& ev : used) {
     CU_TRY(cudaEventSynchronize(ev.second));
     float ms = 0.0f;
     CU_TRY(cudaEventElapsedTime(&ms, ev.first, ev.second));
@@ -1334,8 +1339,233 @@ ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches) {
     g_prof.spare.push_back(ev);
   }
   if (kernel_ms) *kernel_ms = total;
-  if (launches) *launches = static_cast<int64_t>(g_prof.used.size());
-  g_prof.used.clear();
+  if (launches) *launches = static_cast<int64_t>(used.size());
+  used.clear();
+  return IFCM_OK;
+}
+
+ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches) {
+  return ifcm_profile_read_kind(IFCM_PROF_STENCIL, kernel_ms, launches);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- differentiation
+namespace {
+
+// Plan of a launch without timing: a forced plan, the tuning cache, else the rule.
+StencilPlan peek_plan(const BatchVol* vols, int n, const ifcm_params* p) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  if (g_tune.force.np > 0 && stencil_np_supported(p->c, g_tune.force.np)) return g_tune.force;
+  auto it = g_tune.cache.find(plan_key(vols, n, p->c, p->u_dtype));
+  if (it != g_tune.cache.end()) return it->second;
+  return heuristic_plan(vols, n, p->c, is_bf16(p));
+}
+
+// Scratch of a gradient evaluation: the run state of one particle, the
+// checkpoints U^1 .. U^K, the trace of C^{t+1}, S0^{t+1}, J^t, and the reverse
+// pass's coefficient planes, adjoint ping-pong and partial sums.
+struct GradBufs {
+  DevStatus* status;
+  RunBufs run;
+  float* ckpt;          // [K][c][plane]
+  double* trace;        // [K][2c+1]
+  float* A;             // [c][plane]
+  float* B;             // [c][plane]
+  float* e;             // [plane]
+  float* ubar[2];       // [c][plane] each
+  double* partials;     // [blocks][2+c]
+  double* cbar;         // [c]
+  double* best;         // polish: lambda*, xi*, J*
+  double* grad;         // polish: gradient at the current point
+  double* J;            // polish: J at the current point
+};
+
+GradBufs carve_grad(Carver& cv, const ifcm_shape& s, int c, int K) {
+  GradBufs g;
+  const size_t pl = plane_elems(s);
+  const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  g.status = carve_status(cv);
+  g.run = carve_run(cv, s, c, 1, false);
+  g.ckpt = cv.take<float>(static_cast<size_t>(K) * c * pl);
+  g.trace = cv.take<double>(static_cast<size_t>(K) * (2 * c + 1));
+  g.A = cv.take<float>(static_cast<size_t>(c) * pl);
+  g.B = cv.take<float>(static_cast<size_t>(c) * pl);
+  g.e = cv.take<float>(pl);
+  g.ubar[0] = cv.take<float>(static_cast<size_t>(c) * pl);
+  g.ubar[1] = cv.take<float>(static_cast<size_t>(c) * pl);
+  g.partials = cv.take<double>(static_cast<size_t>(adjoint_blocks(nvox)) * (2 + c));
+  g.cbar = cv.take<double>(c);
+  g.best = cv.take<double>(3);
+  g.grad = cv.take<double>(2);
+  g.J = cv.take<double>(1);
+  return g;
+}
+
+// K iterations of one run from (u0, c0) with the stencil kernel: U^{t+1} into
+// checkpoint t, C^{t+1}, S0^{t+1}, J^t into the trace, J^{K-1} into J_out.
+ifcm_status grad_forward(const float* x, const ifcm_shape& s, const ifcm_params* p, int K,
+                         const double* lam_xi, const float* u0, const double* c0, GradBufs& g,
+                         double* J_out, cudaStream_t st) {
+  const int c = p->c;
+  const size_t pl = plane_elems(s);
+  ifcm_params pk = *p;
+  pk.max_iter = K;
+  pk.eps_u = 0.0;
+  RunBufs& rb = g.run;
+  CU_TRY(launch_run_init(c, 1, c0, rb.st, nullptr, st));
+  BatchVol bv{x, s, 1, lam_xi, u0, c0, J_out, nullptr, nullptr};
+  const StencilPlan plan = peek_plan(&bv, 1, &pk);
+  rb.np = plan.np;
+  ReduceArgs r{};
+  r.n_vol = 1;
+  r.P_total = 1;
+  r.partials = rb.partials;
+  r.dmax = rb.dmax;
+  r.st = rb.st;
+  r.max_iter = K;
+  r.eps = 0.0;
+  r.reduce = p->reduce;
+  r.status = g.status;
+  r.vol[0].P = 1;
+  r.vol[0].n_rec = tiling(s, plan.chunks).n_tiles;
+  r.vol[0].rec_base = rb.rec_base[0];
+  r.vol[0].nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  r.vol[0].fitness = J_out;
+  r.vol[0].trace = g.trace;
+  std::vector<StencilArgs> args(1);
+  const int grid = plan_grid(c, false, plan, plan_items(&bv, 1, plan));
+  for (int t = 0; t < K; ++t) {
+    bv.u0 = t == 0 ? u0 : g.ckpt + static_cast<size_t>(t - 1) * c * pl;
+    rb.ua[0] = g.ckpt + static_cast<size_t>(t) * c * pl;
+    ST_TRY(build_args(args[0], &bv, 1, &pk, rb, plan, 0, g.status));
+    cudaEvent_t ev_end = nullptr;
+    cudaEvent_t ev_beg = prof_begin(st, &ev_end);
+    CU_TRY(launch_stencil(c, plan.np, false, args[0], grid, st));
+    if (ev_beg) cudaEventRecord(ev_end, st);
+    CU_TRY(launch_reduce(c, r, st));
+  }
+  return IFCM_OK;
+}
+
+// Reverse pass over the K iterations grad_forward recorded: grad = (dJ/dlambda,
+// dJ/dxi) of J^{K-1}.
+ifcm_status grad_reverse(const float* x, const ifcm_shape& s, const ifcm_params* p, int K,
+                         const double* lam_xi, const float* u0, const double* c0, GradBufs& g,
+                         double* grad, cudaStream_t st) {
+  const int c = p->c;
+  const size_t pl = plane_elems(s);
+  const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+  const int blocks = adjoint_blocks(nvox);
+  const size_t tw = 2 * c + 1;
+  CU_TRY(cudaMemsetAsync(grad, 0, 2 * sizeof(double), st));
+  AdjointArgs a{};
+  a.nx = s.nx;
+  a.ny = s.ny;
+  a.nz = s.nz;
+  a.pitch = s.pitch_x;
+  a.x = x;
+  a.lam_xi = lam_xi;
+  a.A = g.A;
+  a.B = g.B;
+  a.e = g.e;
+  a.partials = g.partials;
+  a.dist_floor = static_cast<float>(p->dist_floor);
+  a.m = static_cast<float>(p->m);
+  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
+  a.m_is_2 = p->m == 2.0;
+  for (int t = K - 1; t >= 0; --t) {
+    a.u = t == 0 ? u0 : g.ckpt + static_cast<size_t>(t - 1) * c * pl;
+    a.ubar_next = t == K - 1 ? nullptr : g.ubar[(t + 1) & 1];
+    a.c_t = t == 0 ? c0 : g.trace + static_cast<size_t>(t - 1) * tw;
+    a.c_next = g.trace + static_cast<size_t>(t) * tw;
+    a.s0_next = a.c_next + c;
+    a.cbar_next = t == K - 1 ? nullptr : g.cbar;
+    a.J_bar = t == K - 1 ? 1.0f : 0.0f;
+    a.ubar_out = g.ubar[t & 1];
+    cudaEvent_t ev_end = nullptr;
+    cudaEvent_t ev_beg = prof_begin(st, &ev_end, IFCM_PROF_ADJOINT_POINT);
+    CU_TRY(launch_adjoint_point(c, a, blocks, st));
+    if (ev_beg) cudaEventRecord(ev_end, st);
+    CU_TRY(launch_adjoint_reduce(c, g.partials, blocks, grad, g.cbar, st));
+    if (t > 0) {
+      ev_beg = prof_begin(st, &ev_end, IFCM_PROF_ADJOINT_GATHER);
+      CU_TRY(launch_adjoint_gather(c, a, blocks, st));
+      if (ev_beg) cudaEventRecord(ev_end, st);
+    }
+  }
+  return IFCM_OK;
+}
+
+ifcm_status check_grad(const float* x, const ifcm_shape& shape, const ifcm_params* p, int K,
+                       const double* lam_xi, const float* u0, const double* c0, const void* ws) {
+  ST_TRY(check_shape(shape));
+  ST_TRY(check_params(p));
+  if (p->u_dtype != IFCM_U_FP32)
+    return fail(IFCM_ERR_UNSUPPORTED, "gradients are built for FP32 memberships only");
+  ST_TRY(check_extent(shape, p));
+  if (K < 1) return fail(IFCM_ERR_INVALID, "K = %d must be >= 1", K);
+  ST_TRY(check_aligned(x, "x"));
+  ST_TRY(check_aligned(u0, "u0"));
+  ST_TRY(check_aligned(ws, "ws"));
+  if (!lam_xi || !c0) return fail(IFCM_ERR_INVALID, "lam_xi and c0 must not be NULL");
+  return IFCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ifcm_grad_workspace_bytes(ifcm_shape shape, const ifcm_params* p, int32_t K) {
+  if (!p || p->c < 2 || p->c > kMaxC || K < 1) return 0;
+  Carver cv(nullptr);
+  carve_grad(cv, shape, p->c, K);
+  return cv.off + 256;
+}
+
+ifcm_status ifcm_grad(const float* x, ifcm_shape shape, const ifcm_params* p, int32_t K,
+                      const double* lam_xi, const float* u0, const double* c0, double* J_out,
+                      double* grad_out, void* ws, size_t ws_bytes, void* stream) {
+  ST_TRY(check_grad(x, shape, p, K, lam_xi, u0, c0, ws));
+  if (!grad_out) return fail(IFCM_ERR_INVALID, "grad_out is NULL");
+  const size_t need = ifcm_grad_workspace_bytes(shape, p, K);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  GradBufs g = carve_grad(cv, shape, p->c, K);
+  CU_TRY(cudaMemsetAsync(g.status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(g.run.st.updates, 0, sizeof(unsigned long long), st));
+  ST_TRY(grad_forward(x, shape, p, K, lam_xi, u0, c0, g, J_out ? J_out : g.J, st));
+  ST_TRY(grad_reverse(x, shape, p, K, lam_xi, u0, c0, g, grad_out, st));
+  return IFCM_OK;
+}
+
+ifcm_status ifcm_polish(const float* x, ifcm_shape shape, const ifcm_params* p, int32_t K,
+                        int32_t steps, double step0, double decay, double* lam_xi,
+                        const float* u0, const double* c0, double* J_out, void* ws,
+                        size_t ws_bytes, void* stream) {
+  ST_TRY(check_grad(x, shape, p, K, lam_xi, u0, c0, ws));
+  if (steps < 0) return fail(IFCM_ERR_INVALID, "steps = %d must be >= 0", steps);
+  if (!(step0 > 0.0) || !(decay > 0.0) || !(decay <= 1.0))
+    return fail(IFCM_ERR_INVALID, "step0 must be > 0 and decay in (0, 1]");
+  const size_t need = ifcm_grad_workspace_bytes(shape, p, K);
+  if (ws_bytes < need) return fail(IFCM_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  GradBufs g = carve_grad(cv, shape, p->c, K);
+  CU_TRY(cudaMemsetAsync(g.status, 0, sizeof(DevStatus), st));
+  CU_TRY(cudaMemsetAsync(g.run.st.updates, 0, sizeof(unsigned long long), st));
+  CU_TRY(launch_polish_step(lam_xi, g.grad, g.J, g.best, 0.0, 0, st));
+  double alpha = step0;
+  for (int k = 0; k < steps; ++k, alpha *= decay) {
+    ST_TRY(grad_forward(x, shape, p, K, lam_xi, u0, c0, g, g.J, st));
+    ST_TRY(grad_reverse(x, shape, p, K, lam_xi, u0, c0, g, g.grad, st));
+    CU_TRY(launch_polish_step(lam_xi, g.grad, g.J, g.best, alpha, 1, st));
+  }
+  ST_TRY(grad_forward(x, shape, p, K, lam_xi, u0, c0, g, g.J, st));
+  CU_TRY(launch_polish_step(lam_xi, g.grad, g.J, g.best, 0.0, 2, st));
+  if (J_out)
+    CU_TRY(cudaMemcpyAsync(J_out, g.best + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
   return IFCM_OK;
 }
 

@@ -193,6 +193,15 @@ __device__ __noinline__ void reduce_comp32(const ReduceArgs& a, const ReduceVol&
     a.st.J[gp] = J;
     const int it = a.st.iters[gp] + 1;
     a.st.iters[gp] = it;
+    if (rv.trace && it <= a.max_iter) {
+      double* tr = rv.trace + (static_cast<size_t>(p) * a.max_iter + (it - 1)) * (2 * C + 1);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        tr[j] = cen[j];
+        tr[C + j] = static_cast<double>(__fadd_rn(s_hi[j][0], s_lo[j][0]));
+      }
+      tr[2 * C] = J;
+    }
     if (rv.fitness) rv.fitness[p] = J;
     if (rv.iters_out) rv.iters_out[p] = it;
     const double delta = static_cast<double>(s_mx[0]);
@@ -252,6 +261,15 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
     a.st.J[gp] = J;
     const int it = a.st.iters[gp] + 1;
     a.st.iters[gp] = it;
+    if (rv.trace && it <= a.max_iter) {    // C^{t+1}, S0^{t+1}, J^t for the reverse pass
+      double* tr = rv.trace + (static_cast<size_t>(p) * a.max_iter + (it - 1)) * (2 * C + 1);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        tr[j] = cen[j];
+        tr[C + j] = s_sum[j][0];
+      }
+      tr[2 * C] = J;
+    }
     if (rv.fitness) rv.fitness[p] = J;
     if (rv.iters_out) rv.iters_out[p] = it;
     const double delta = static_cast<double>(s_max[0]);

@@ -101,6 +101,7 @@ struct ReduceVol {
   double* fitness;              // [P] or NULL
   int32_t* iters_out;           // [P] or NULL
   double* c_out;                // [P][c] or NULL
+  double* trace;                // [P][max_iter][2c+1] C^{t+1}, S0^{t+1}, J^t, or NULL
 };
 
 struct ReduceArgs {
@@ -117,6 +118,38 @@ struct ReduceArgs {
 };
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s);
+
+// ------------------------------------------------ reverse pass (adjoint.cu)
+// One iteration t of the reverse pass over K unrolled IFCM iterations.
+struct AdjointArgs {
+  int nx, ny, nz, pitch;
+  const float* x;               // normalised volume
+  const float* u;               // U^t (checkpoint)
+  const float* ubar_next;       // adjoint of U^{t+1}, or NULL (zero)
+  const double* lam_xi;         // device (lambda, xi)
+  const double* c_t;            // C^t [c]
+  const double* c_next;         // C^{t+1} [c]
+  const double* s0_next;        // S0^{t+1} = sum_i u^m [c]
+  const double* cbar_next;      // adjoint of C^{t+1} [c], or NULL (zero)
+  float J_bar;                  // dL/dJ^t: 1 for the last iteration, else 0
+  float* A;                     // [c][plane] H_bar / G (point kernel out, gather in)
+  float* B;                     // [c][plane] F_bar / Q
+  float* e;                     // [plane] 1 where G = 0 (flat neighbourhood)
+  float* ubar_out;              // [c][plane] adjoint of U^t (gather kernel out)
+  double* partials;             // [blocks][2 + c] lambda_bar, xi_bar, c_bar^t
+  float dist_floor, m, inv_m1;
+  int m_is_2;
+};
+
+int adjoint_blocks(long long nvox);
+cudaError_t launch_adjoint_point(int c, const AdjointArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_reduce(int c, const double* partials, int blocks, double* grad,
+                                  double* cbar_out, cudaStream_t s);
+// mode 0: start (best = current, +inf); 1: keep the best, take a step; 2: keep
+// the best and write it to lam_xi.
+cudaError_t launch_polish_step(double* lam_xi, const double* grad, const double* J, double* best,
+                               double alpha, int mode, cudaStream_t s);
 
 // ------------------------------------------------------- auxiliary kernels
 cudaError_t launch_run_init(int c, int P, const double* c0, RunState st, double* J_clear,

@@ -320,6 +320,74 @@ def pso_fitness_multi(volumes, params, ws=None):
     return outs
 
 
+# ------------------------------------------- d J / d (lambda, xi) and polish
+def ifcm_grad_workspace_bytes(x, params, K, nx=None):
+    p = params.native()
+    return N.load().ifcm_grad_workspace_bytes(shape_of(x, nx), ctypes.byref(p), int(K))
+
+
+def ifcm_grad(x, params, lam_xi, u0, c0, K, nx=None, ws=None):
+    """(J^{K-1}, tensor [dJ/dlambda, dJ/dxi]) of K unrolled IFCM iterations
+    from (u0, c0) at (lambda, xi).  Both results stay on the device."""
+    lib = N.load()
+    _check_cuda(x, torch.float32, "x")
+    _check_cuda(u0, torch.float32, "u0")
+    dev = x.device
+    lx = _lam_xi_tensor(lam_xi, dev)
+    c0 = _lam_xi_tensor(c0, dev)
+    shp = shape_of(x, nx)
+    p = params.native()
+    J = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(2, dtype=torch.float64, device=dev)
+    need = lib.ifcm_grad_workspace_bytes(shp, ctypes.byref(p), int(K))
+    ws = workspace(need, dev) if ws is None else ws
+    N.check(lib.ifcm_grad(_ptr(x), shp, ctypes.byref(p), int(K), _ptr(lx), _ptr(u0), _ptr(c0),
+                          _ptr(J), _ptr(g), _ptr(ws), ws.numel(), _stream()))
+    return J[0], g
+
+
+def ifcm_polish(x, params, lam_xi, u0, c0, K, steps=10, step0=0.05, decay=0.7, nx=None,
+                ws=None):
+    """Projected gradient polishing from lam_xi; returns (best (lambda, xi)
+    as a device tensor, its J^{K-1})."""
+    lib = N.load()
+    _check_cuda(x, torch.float32, "x")
+    _check_cuda(u0, torch.float32, "u0")
+    dev = x.device
+    lx = _lam_xi_tensor(lam_xi, dev).clone()
+    c0 = _lam_xi_tensor(c0, dev)
+    shp = shape_of(x, nx)
+    p = params.native()
+    J = torch.empty(1, dtype=torch.float64, device=dev)
+    need = lib.ifcm_grad_workspace_bytes(shp, ctypes.byref(p), int(K))
+    ws = workspace(need, dev) if ws is None else ws
+    N.check(lib.ifcm_polish(_ptr(x), shp, ctypes.byref(p), int(K), int(steps), float(step0),
+                            float(decay), _ptr(lx), _ptr(u0), _ptr(c0), _ptr(J), _ptr(ws),
+                            ws.numel(), _stream()))
+    return lx, float(J[0])
+
+
+class IFCMObjective(torch.autograd.Function):
+    """J^{K-1}(lambda, xi) as a differentiable function of a CUDA float64
+    tensor lam_xi of shape (2,).  ``forward`` runs the checkpointed forward
+    pass and the adjoint kernels together (``ifcm_grad``) and keeps the
+    gradient; ``backward`` scales it by the incoming gradient.
+
+        J = IFCMObjective.apply(lam_xi, x, u0, c0, params, K, nx)
+    """
+
+    @staticmethod
+    def forward(ctx, lam_xi, x, u0, c0, params, K, nx=None):
+        J, g = ifcm_grad(x, params, lam_xi.detach().contiguous(), u0, c0, K, nx=nx)
+        ctx.save_for_backward(g)
+        return J.clone()
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return gJ * g, None, None, None, None, None, None
+
+
 # ------------------------------------------------------ Alg 1 steps 3, 5-8
 class Swarm:
     """Device-resident swarm; ``init`` is step 3, ``step`` steps 5-8."""
@@ -423,8 +491,13 @@ def profile_enable(on=True):
     N.load().ifcm_profile_enable(1 if on else 0)
 
 
-def profile_read():
+PROF_STENCIL, PROF_ADJOINT_POINT, PROF_ADJOINT_GATHER = 0, 1, 2
+
+
+def profile_read(kind=PROF_STENCIL):
+    """(summed kernel ms, launches) recorded for one kind of kernel since the
+    last read of that kind."""
     ms = ctypes.c_double(0.0)
     n = ctypes.c_int64(0)
-    N.check(N.load().ifcm_profile_read(ctypes.byref(ms), ctypes.byref(n)))
+    N.check(N.load().ifcm_profile_read_kind(int(kind), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value

@@ -106,8 +106,16 @@ SIGNATURES = {
     "ifcm_fit_noalloc": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p]),
+    "ifcm_grad_workspace_bytes": (c_size_t, [IfcmShape, POINTER(IfcmParams), c_int32]),
+    "ifcm_grad": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), c_int32, c_void_p,
+                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                            c_void_p]),
+    "ifcm_polish": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), c_int32, c_int32,
+                              c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_size_t, c_void_p]),
     "ifcm_profile_enable": (None, [c_int32]),
     "ifcm_profile_read": (c_int32, [POINTER(c_double), POINTER(c_int64)]),
+    "ifcm_profile_read_kind": (c_int32, [c_int32, POINTER(c_double), POINTER(c_int64)]),
 }
 
 _lib = None

@@ -131,6 +131,16 @@ def multi_tissue(shape=(256, 256, 256), seed=5, sigma=0.1,
     return rician(img, sigma, rng).astype(np.float32)
 
 
+def gaussian_phantom(shape=(128, 128, 128), seed=4, sigma=0.09):
+    """Brain-like nested ellipsoids (0/0.25/0.55/0.85, no bias) plus i.i.d.
+    Gaussian noise (the c = 4 differentiation workload)."""
+    nz, ny, nx = shape
+    ax = [(fz * nz, fy * ny, fx * nx) for fz, fy, fx in BRAIN_RADII]
+    img = nested_ellipsoids(shape, BRAIN_LEVELS, ax)
+    rng = np.random.default_rng(seed)
+    return gaussian(img, sigma, rng).astype(np.float32)
+
+
 def piecewise_cube(n=4, levels=(0.0, 1.0), seed=None, sigma=0.0, nz=None):
     """Tiny noise-free (or lightly noisy) piecewise-constant volume whose
     classes split along x: used by brute-force and fixed-point tests."""
