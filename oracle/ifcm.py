@@ -34,6 +34,12 @@ R10 [Alg 1 s2]   the unspecified "Modified_FCM with Gaussian mixture
 Shells [Eq 9, Eq 10]  NB is the set of Eq 9 (L = 3: the 26 voxels around
                  x_i in 3D, 8 in 2D); shell S_r holds the members at
                  Chebyshev distance r, r = 1..V, with W_r of Eq 10.
+R17 [Eq 9, Eq 10]  Eq 10 makes V "the distance of the furthest voxel", but
+                 Eq 9's ball with L = 3 holds only distance-1 voxels.  For V
+                 shells L is the smallest value whose ball contains the whole
+                 cube of Chebyshev radius V (2^(L-1) > 3 V^2): L = 3 for V = 1,
+                 5 for V = 2, 6 for V = 3.  The neighbourhood is that
+                 cube without its centre, and S_r is its shell at distance r.
 """
 import math
 
@@ -57,6 +63,15 @@ def normalize(vol):
 # --------------------------------------------------------------------------
 # Eq 9 (neighbourhood), Eq 10 (shell weights)
 # --------------------------------------------------------------------------
+def cube_L(V):
+    """Smallest L of Eq 9 whose ball holds the cube of Chebyshev radius V
+    (reading R17): 2^(L-1) > 3 V^2."""
+    L = 1
+    while 2 ** (L - 1) <= 3 * V * V:
+        L += 1
+    return L
+
+
 def neighbourhood(L=3):
     """Offsets (dz, dy, dx) with 0 < dx^2 + dy^2 + dz^2 < 2^(L-1)  (Eq 9)."""
     bound = 2 ** (L - 1)
@@ -71,9 +86,10 @@ def neighbourhood(L=3):
     return offs
 
 
-def shells(V=1, L=3):
-    """S_r = members of NB at Chebyshev distance r, for r = 1..V."""
-    nb = neighbourhood(L)
+def shells(V=1, L=None):
+    """S_r = members of NB at Chebyshev distance r, for r = 1..V (L defaults
+    to cube_L(V), reading R17)."""
+    nb = neighbourhood(cube_L(V) if L is None else L)
     return [[o for o in nb if max(abs(o[0]), abs(o[1]), abs(o[2])) == r]
             for r in range(1, V + 1)]
 
@@ -94,7 +110,7 @@ def _overlap(n, d):
 # --------------------------------------------------------------------------
 # Eqs 5-8: neighbourhood terms H and F
 # --------------------------------------------------------------------------
-def neighbour_terms(x, U, V=1, h=1.0, L=3, return_aux=False):
+def neighbour_terms(x, U, V=1, h=1.0, L=None, return_aux=False):
     """H_ij (Eq 5, with g of Eq 6) and F_ij (Eq 7, with q^2 of Eq 8).
 
     Returns (H, F) of shape (c, nz, ny, nx); with ``return_aux`` also a dict

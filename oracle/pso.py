@@ -106,19 +106,40 @@ def fitness_batch(x, U0, C0, lam_xi, m=2.0, max_iter=50, eps=1e-5, V=1, h=1.0,
     return np.array(out), np.array(iters)
 
 
+def fitness_onestep(x, states, lam_xi, m=2.0, V=1, h=1.0, dist_floor=1e-12):
+    """Step 4 in the paper's one-step reading of Algorithm 2 (steps 6-11):
+    each particle carries its own (U, C) from generation to generation and
+    advances it by one IFCM iteration at its current (lambda, xi); the
+    fitness is that iteration's J.  ``states`` is a list of (U, C), updated
+    in place."""
+    out = []
+    for p, (lam, xi) in enumerate(np.asarray(lam_xi, dtype=np.float64)):
+        U, C = states[p]
+        U, C, J, _ = ifcm.ifcm_iteration(x, U, C, lam, xi, m, V, h, dist_floor)
+        states[p] = (U, C)
+        out.append(J)
+    return np.array(out)
+
+
 def pifcm3d(vol, c, P, generations, seed, m=2.0, max_iter=50, eps=1e-5,
             init_max_iter=300, vmax=0.2, radius=1, V=1, h=1.0, z=None,
-            dist_floor=1e-12):
+            dist_floor=1e-12, fitness="restart"):
     """Algorithm 1 end to end: normalise (Alg 2 step 1), optional slice z
     (Alg 1 step 1), FCM start (step 2), swarm (steps 3-9), final IFCM at the
-    best particle (step 11).  Returns a dict with U, C, lambda, xi, J."""
+    best particle (step 11).  ``fitness`` is "restart" (reading R5: an IFCM
+    run from (U0, C0) per evaluation) or "onestep" (``fitness_onestep``).
+    Returns a dict with U, C, lambda, xi, J."""
     x = ifcm.normalize(vol)
     if z is not None:
         x = x[z:z + 1]
     U0, C0, _, init_iters = ifcm.fcm_init(x, c, m, init_max_iter, eps, dist_floor)
     s = Swarm(P, seed, vmax, radius)
+    states = [(U0, C0)] * P
     for _ in range(generations):
-        f, _ = fitness_batch(x, U0, C0, s.x, m, max_iter, eps, V, h, dist_floor)
+        if fitness == "onestep":
+            f = fitness_onestep(x, states, s.x, m, V, h, dist_floor)
+        else:
+            f, _ = fitness_batch(x, U0, C0, s.x, m, max_iter, eps, V, h, dist_floor)
         pso_step(s, f)
     b = best_particle(s)
     lam, xi = s.pbest_x[b]

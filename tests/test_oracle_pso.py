@@ -101,3 +101,21 @@ def test_pifcm3d_small_end_to_end():
     assert np.all(np.diff(np.sort(C)) > 0.1)          # four distinct grey levels
     assert 0 <= out["lambda"] <= 1 and 0 <= out["xi"] <= 1
     assert out["J"] <= out["pbest_f"].min() * (1 + 1e-12) + 1e-15
+
+
+
+def test_onestep_fitness_carries_each_particle_state():
+    # with positions held fixed, generation g of the one-step reading is
+    # iteration g of an IFCM run from the shared start
+    from oracle import ifcm
+    rng = np.random.default_rng(21)
+    x = np.clip(np.repeat([0.1, 0.5, 0.9], 24).reshape(3, 4, 6) +
+                0.04 * rng.standard_normal((3, 4, 6)), 0, 1)
+    U0, C0, _, _ = ifcm.fcm_init(x, 3, max_iter=20)
+    lam_xi = np.array([[0.3, 0.2], [0.6, 0.1]])
+    states = [(U0, C0)] * 2
+    for g in range(4):
+        f = pso.fitness_onestep(x, states, lam_xi)
+        for p in range(2):
+            J = ifcm.ifcm_fit(x, U0, C0, lam_xi[p, 0], lam_xi[p, 1], 2.0, g + 1, 0.0)[2]
+            assert f[p] == J

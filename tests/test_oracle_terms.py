@@ -248,3 +248,84 @@ def test_lambda_xi_signs():
     assert abs(dl[0, 0, 0, 0] - 0.09 * 0.6) < 1e-16 and abs(dl[1, 0, 0, 0] - 0.25 * 0.9) < 1e-16
     assert abs(dx_[0, 0, 0, 0] - 0.09 * 0.95) < 1e-16 and abs(dx_[1, 0, 0, 0] - 0.25 * 0.7) < 1e-16
     assert np.allclose(d0[:, 0, 0, 0], [0.09, 0.25])
+
+
+# ----------------------------------------------- V > 1 shells (Eq 10, R17)
+def test_cube_L_and_shell_sizes():
+    assert [ifcm.cube_L(v) for v in (1, 2, 3, 4)] == [3, 5, 6, 7]
+    for V in (1, 2, 3):
+        sh = ifcm.shells(V)
+        assert [len(s) for s in sh] == [(2 * r + 1) ** 3 - (2 * r - 1) ** 3
+                                        for r in range(1, V + 1)]
+        for r, s in enumerate(sh, start=1):
+            assert all(max(abs(a) for a in o) == r for o in s)
+    # with Eq 9's L = 3 the second shell is empty (the ball holds distance 1 only)
+    assert len(ifcm.shells(2, L=3)[1]) == 0
+
+
+def test_interior_Q_of_the_second_shell():
+    # sum of dx^2 + dy^2 + dz^2 over the 5^3 cube is 3 * 10 * 25 = 750; the
+    # inner 3^3 cube contributes 3 * 2 * 9 = 54; so Q_2 = 696 at an interior voxel
+    x = np.random.default_rng(0).random((5, 5, 5))
+    U = np.full((2, 5, 5, 5), 0.5)
+    _, _, aux = ifcm.neighbour_terms(x, U, V=2, return_aux=True)
+    assert aux["Q"][0][2, 2, 2] == 54 and aux["Q"][1][2, 2, 2] == 696
+    assert aux["count"][1][2, 2, 2] == 98
+
+
+def _brute_terms_V(x, U, V, h):
+    """Per-voxel loops over the cube of radius V, shell by shell, with the
+    weights of Eq 10 renormalised over the shells that hold an in-volume voxel."""
+    c = U.shape[0]
+    nz, ny, nx = x.shape
+    W = np.array([np.exp(-r / h) for r in range(1, V + 1)])
+    W = W / W.sum()
+    H = np.zeros_like(U)
+    F = np.zeros_like(U)
+    rng = range(-V, V + 1)
+    for z, y, xx in itertools.product(range(nz), range(ny), range(nx)):
+        hs, fs, ws = np.zeros(c), np.zeros(c), 0.0
+        for r in range(1, V + 1):
+            G = Q = 0.0
+            n = 0
+            hh, ff, ss = np.zeros(c), np.zeros(c), np.zeros(c)
+            for dz, dy, dx in itertools.product(rng, rng, rng):
+                if max(abs(dz), abs(dy), abs(dx)) != r:
+                    continue
+                kz, ky, kx = z + dz, y + dy, xx + dx
+                if not (0 <= kz < nz and 0 <= ky < ny and 0 <= kx < nx):
+                    continue
+                gk = abs(x[z, y, xx] - x[kz, ky, kx])
+                qk = dx * dx + dy * dy + dz * dz
+                hh += U[:, kz, ky, kx] * gk
+                ff += U[:, kz, ky, kx] ** 2 * qk
+                ss += U[:, kz, ky, kx]
+                G += gk
+                Q += qk
+                n += 1
+            if n:
+                hs += W[r - 1] * (hh / G if G > 0 else ss / n)
+                fs += W[r - 1] * ff / Q
+                ws += W[r - 1]
+        if ws > 0:
+            H[:, z, y, xx] = hs / ws
+            F[:, z, y, xx] = fs / ws
+    return H, F
+
+
+@pytest.mark.parametrize("shape,V,h", [((5, 6, 7), 2, 1.0), ((1, 8, 9), 2, 0.5),
+                                       ((4, 7, 7), 3, 2.0), ((2, 3, 9), 2, 1.0)])
+def test_shells_match_brute_force_loops(shape, V, h):
+    x, U = _random_case(shape, 3, 6)
+    H, F = ifcm.neighbour_terms(x, U, V=V, h=h)
+    Hb, Fb = _brute_terms_V(x, U, V, h)
+    assert np.allclose(H, Hb, atol=1e-14)
+    assert np.allclose(F, Fb, atol=1e-14)
+    assert np.allclose(H.sum(axis=0), 1.0, atol=1e-13)
+
+
+def test_shells_uniform_memberships():
+    x = np.random.default_rng(1).random((4, 6, 5))
+    U = np.full((4,) + x.shape, 0.25)
+    H, F = ifcm.neighbour_terms(x, U, V=3, h=1.5)
+    assert np.allclose(H, 0.25, atol=1e-15) and np.allclose(F, 0.0625, atol=1e-15)
