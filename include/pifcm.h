@@ -113,7 +113,19 @@ typedef struct {
   uint64_t seed;             /* Philox key                                        */
   int32_t init_max_iter;     /* iterations of the FCM start (Algorithm 1 step 2)  */
   int32_t slice_z;           /* -1: whole volume; else segment slice z as 2D (Algorithm 1 step 1) */
+  int32_t fitness_mode;      /* PIFCM_FITNESS_RESTART or PIFCM_FITNESS_ONESTEP     */
 } pifcm_options;
+
+/* What one fitness evaluation (Algorithm 1 step 4) is.
+ * PIFCM_FITNESS_RESTART (reading R5): an IFCM run from the shared FCM start
+ *   until max|du| < eps_u or max_iter iterations; fitness = its last J.
+ * PIFCM_FITNESS_ONESTEP (Algorithm 2 steps 6-11 read literally): every
+ *   particle keeps its own (U, C), starting from the FCM start, and each
+ *   generation advances it by one IFCM iteration at the particle's current
+ *   (lambda, xi); fitness = that iteration's J.  max_iter and eps_u then
+ *   apply only to the final run (Algorithm 1 step 11). */
+#define PIFCM_FITNESS_RESTART 0
+#define PIFCM_FITNESS_ONESTEP 1
 
 /* Result block written by pifcm3d (device or host copy). */
 typedef struct {

@@ -58,8 +58,12 @@ ifcm_status check_params(const ifcm_params* p) {
   if (p->c < 2 || p->c > kMaxC) return fail(IFCM_ERR_INVALID, "c = %d outside 2..%d", p->c, kMaxC);
   if (!(p->m > 1.0) || !std::isfinite(p->m))
     return fail(IFCM_ERR_INVALID, "fuzzifier m = %g must be finite and > 1", p->m);
-  if (p->V != 1)
-    return fail(IFCM_ERR_UNSUPPORTED, "V = %d shells: only V = 1 is built", p->V);
+  if (p->V < 1 || p->V > kMaxV)
+    return fail(IFCM_ERR_UNSUPPORTED, "V = %d shells: 1..%d are built", p->V, kMaxV);
+  if (p->V > 1 && (!(p->h > 0.0) || !std::isfinite(p->h)))
+    return fail(IFCM_ERR_INVALID, "h = %g must be finite and > 0 for V > 1", p->h);
+  if (p->V > 1 && p->u_dtype != IFCM_U_FP32)
+    return fail(IFCM_ERR_UNSUPPORTED, "V > 1 shells are built for FP32 memberships only");
   if (p->max_iter < 1) return fail(IFCM_ERR_INVALID, "max_iter = %d must be >= 1", p->max_iter);
   if (!(p->eps_u >= 0.0)) return fail(IFCM_ERR_INVALID, "eps_u = %g must be >= 0", p->eps_u);
   if (!(p->dist_floor > 0.0) || !(p->dist_floor < 1.0))
@@ -550,55 +554,125 @@ ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const
   return IFCM_OK;
 }
 
-// IFCM runs of every particle of n volumes (same c, n <= kMaxVols) with the
-// stencil kernel: one launch per iteration covers all volumes' work items.
+void fill_plain_method(PlainArgs& a, const ifcm_params* p);
+
+// A prepared batch of IFCM runs of every particle of n volumes (same c,
+// n <= kMaxVols): run state initialised from each volume's c0, the launch
+// plan, the three parameter blocks of the stencil kernel (iteration 0: U0 ->
+// ua, odd: ua -> ub, even: ub -> ua) or, for V > 1 shells, of the plain
+// kernel, and the per-particle finalisation.  iteration(it) queues one
+// iteration of every running particle.
+struct BatchRun {
+  const BatchVol* vols = nullptr;
+  int n = 0;
+  const ifcm_params* p = nullptr;
+  RunBufs* rb = nullptr;
+  DevStatus* status = nullptr;
+  bool wide = false;                 // V > 1: plain kernel
+  StencilPlan pl{1, 1};
+  std::vector<StencilArgs> args;
+  int grid = 1;
+  ReduceArgs r{};
+
+  ifcm_status prepare(const BatchVol* vols_, int n_, const ifcm_params* p_, RunBufs& rb_,
+                      DevStatus* status_, int max_iter, double eps, cudaStream_t st) {
+    vols = vols_;
+    n = n_;
+    p = p_;
+    rb = &rb_;
+    status = status_;
+    wide = p->V > 1;
+    const int c = p->c;
+    int P_total = 0;
+    for (int v = 0; v < n; ++v) {
+      CU_TRY(launch_run_init(c, vols[v].P, vols[v].c0, shifted(rb->st, rb->pbase[v], c),
+                             nullptr, st));
+      P_total += vols[v].P;
+    }
+    if (!wide) {
+      ST_TRY(choose_plan(vols, n, p, *rb, status, st, &pl));
+      rb->np = pl.np;
+      ST_TRY(pack_starts(vols, n, c, *rb, pl.np, st));
+      args.resize(3);
+      for (int k = 0; k < 3; ++k) ST_TRY(build_args(args[k], vols, n, p, *rb, pl, k, status));
+      grid = plan_grid(c, rb->bf16, pl, plan_items(vols, n, pl));
+    } else {
+      rb->np = 1;
+    }
+    r = ReduceArgs{};
+    r.n_vol = n;
+    r.P_total = P_total;
+    r.partials = rb->partials;
+    r.dmax = rb->dmax;
+    r.st = rb->st;
+    r.max_iter = max_iter;
+    r.eps = eps;
+    r.reduce = p->reduce;
+    r.status = status;
+    for (int v = 0; v < n; ++v) {
+      ReduceVol& rv = r.vol[v];
+      const ifcm_shape& s = vols[v].shape;
+      rv.pbase = rb->pbase[v];
+      rv.P = vols[v].P;
+      rv.nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+      rv.n_rec = wide ? plain_blocks(rv.nvox, kPlainVpt) : tiling(s, pl.chunks).n_tiles;
+      rv.rec_base = rb->rec_base[v];
+      rv.fitness = vols[v].fitness;
+      rv.iters_out = vols[v].iters;
+      rv.c_out = vols[v].c_out;
+    }
+    return IFCM_OK;
+  }
+
+  ifcm_status iteration(int it, cudaStream_t st) {
+    const int c = p->c;
+    const int kind = it == 0 ? 0 : (it % 2 == 1 ? 1 : 2);
+    if (!wide) {
+      cudaEvent_t ev_end = nullptr;
+      cudaEvent_t ev_beg = prof_begin(st, &ev_end);
+      CU_TRY(launch_stencil(c, pl.np, rb->bf16, args[kind], grid, st));
+      if (ev_beg) cudaEventRecord(ev_end, st);
+    } else {
+      for (int v = 0; v < n; ++v) {
+        const BatchVol& bv = vols[v];
+        const ifcm_shape& s = bv.shape;
+        const long long plane = static_cast<long long>(plane_elems(s));
+        const int blocks = r.vol[v].n_rec;
+        PlainArgs a{};
+        a.nx = s.nx;
+        a.ny = s.ny;
+        a.nz = s.nz;
+        a.pitch = s.pitch_x;
+        a.x = bv.x;
+        a.u_src = kind == 0 ? bv.u0 : (kind == 1 ? rb->ua[v] : rb->ub[v]);
+        a.src_pstride = kind == 0 ? 0 : c * plane;
+        a.u_dst = kind == 1 ? rb->ub[v] : rb->ua[v];
+        a.dst_pstride = c * plane;
+        a.lam_xi = bv.lam_xi;
+        a.centres = rb->st.centres + static_cast<size_t>(rb->pbase[v]) * c;
+        a.active = rb->st.active + rb->pbase[v];
+        a.partials = rb->partials + static_cast<size_t>(rb->rec_base[v]) * (2 * c + 1);
+        a.dmax = rb->dmax + rb->rec_base[v];
+        fill_plain_method(a, p);
+        a.stencil = 1;
+        a.P = bv.P;
+        a.n_rec = blocks;
+        a.status = status;
+        CU_TRY(launch_plain(c, a, blocks, st));
+      }
+    }
+    CU_TRY(launch_reduce(c, r, st));
+    return IFCM_OK;
+  }
+};
+
+// IFCM runs of every particle of n volumes with the stencil kernel (the plain
+// kernel for V > 1): one launch per iteration covers all volumes' work items.
 ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p, RunBufs& rb,
                               DevStatus* status, cudaStream_t st) {
-  const int c = p->c;
-  int P_total = 0;
-  for (int v = 0; v < n; ++v) {
-    CU_TRY(launch_run_init(c, vols[v].P, vols[v].c0, shifted(rb.st, rb.pbase[v], c), nullptr,
-                           st));
-    P_total += vols[v].P;
-  }
-  StencilPlan pl;
-  ST_TRY(choose_plan(vols, n, p, rb, status, st, &pl));
-  const bool bf = rb.bf16;
-  rb.np = pl.np;
-  ST_TRY(pack_starts(vols, n, c, rb, pl.np, st));
-  // Three parameter blocks: iteration 0 (U0 -> ua), odd (ua -> ub), even (ub -> ua).
-  std::vector<StencilArgs> args(3);
-  for (int k = 0; k < 3; ++k) ST_TRY(build_args(args[k], vols, n, p, rb, pl, k, status));
-  ReduceArgs r{};
-  r.n_vol = n;
-  r.P_total = P_total;
-  r.partials = rb.partials;
-  r.dmax = rb.dmax;
-  r.st = rb.st;
-  r.max_iter = p->max_iter;
-  r.eps = p->eps_u;
-  r.reduce = p->reduce;
-  r.status = status;
-  for (int v = 0; v < n; ++v) {
-    ReduceVol& rv = r.vol[v];
-    rv.pbase = rb.pbase[v];
-    rv.P = vols[v].P;
-    rv.n_rec = tiling(vols[v].shape, pl.chunks).n_tiles;
-    rv.rec_base = rb.rec_base[v];
-    rv.nvox = static_cast<long long>(vols[v].shape.nx) * vols[v].shape.ny * vols[v].shape.nz;
-    rv.fitness = vols[v].fitness;
-    rv.iters_out = vols[v].iters;
-    rv.c_out = vols[v].c_out;
-  }
-  const int grid = plan_grid(c, bf, pl, plan_items(vols, n, pl));
-  for (int it = 0; it < p->max_iter; ++it) {
-    const StencilArgs& a = args[it == 0 ? 0 : (it % 2 == 1 ? 1 : 2)];
-    cudaEvent_t ev_end = nullptr;
-    cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-    CU_TRY(launch_stencil(c, pl.np, bf, a, grid, st));
-    if (ev_beg) cudaEventRecord(ev_end, st);
-    CU_TRY(launch_reduce(c, r, st));
-  }
+  BatchRun br;
+  ST_TRY(br.prepare(vols, n, p, rb, status, p->max_iter, p->eps_u, st));
+  for (int it = 0; it < p->max_iter; ++it) ST_TRY(br.iteration(it, st));
   return IFCM_OK;
 }
 
@@ -609,6 +683,19 @@ ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* 
                         DevStatus* status, cudaStream_t st) {
   BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out};
   return run_stencil_batch(&bv, 1, p, rb, status, st);
+}
+
+// Method constants and Eq 10 weights of a plain-kernel launch.
+void fill_plain_method(PlainArgs& a, const ifcm_params* p) {
+  a.dist_floor = static_cast<float>(p->dist_floor);
+  a.m = static_cast<float>(p->m);
+  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
+  a.m_is_2 = p->m == 2.0;
+  a.vpt = kPlainVpt;
+  a.V = p->V;
+  double e[kMaxV], sum = 0.0;
+  for (int r = 1; r <= p->V; ++r) sum += (e[r - 1] = std::exp(-r / (p->V > 1 ? p->h : 1.0)));
+  for (int r = 1; r <= p->V; ++r) a.W[r - 1] = static_cast<float>(e[r - 1] / sum);
 }
 
 // Particle 0's final memberships (P = 1 runs) as FP32 [c][plane].
@@ -647,12 +734,10 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   a.active = rb.st.active;
   a.partials = rb.partials;
   a.dmax = rb.dmax;
-  a.dist_floor = static_cast<float>(p->dist_floor);
-  a.m = static_cast<float>(p->m);
-  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
-  a.m_is_2 = p->m == 2.0;
-  a.vpt = kPlainVpt;
+  fill_plain_method(a, p);
   a.stencil = stencil ? 1 : 0;
+  a.P = 1;
+  a.n_rec = blocks;
   a.status = status;
   ReduceArgs r{};
   r.n_vol = 1;
@@ -754,6 +839,9 @@ ifcm_status check_options(const pifcm_options* o, const ifcm_shape& s) {
   if (!(o->vmax > 0.0)) return fail(IFCM_ERR_INVALID, "vmax must be > 0");
   if (o->init_max_iter < 1) return fail(IFCM_ERR_INVALID, "init_max_iter must be >= 1");
   if (o->slice_z >= s.nz) return fail(IFCM_ERR_INVALID, "slice_z %d >= nz %d", o->slice_z, s.nz);
+  if (o->fitness_mode != PIFCM_FITNESS_RESTART && o->fitness_mode != PIFCM_FITNESS_ONESTEP)
+    return fail(IFCM_ERR_INVALID, "fitness_mode = %d: expected PIFCM_FITNESS_RESTART or "
+                "PIFCM_FITNESS_ONESTEP", o->fitness_mode);
   return IFCM_OK;
 }
 
@@ -1262,10 +1350,21 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   sw.pbest_f = b.sw_pbf;
   sw.gen = b.sw_gen;
   CU_TRY(launch_pso_init(sw, st));
-  for (int g = 0; g < o->generations; ++g) {
-    ST_TRY(run_stencil(xr, rs, p, sw.x, P, b.u0, b.c0, rb, b.fitness, b.iters, nullptr, b.status,
-                       st));
-    CU_TRY(launch_pso_step(sw, b.fitness, st));
+  if (o->fitness_mode == PIFCM_FITNESS_ONESTEP) {
+    // each particle's (U, C) persists: generation g is iteration g of its run
+    BatchVol bv{xr, rs, P, sw.x, b.u0, b.c0, b.fitness, b.iters, nullptr};
+    BatchRun br;
+    ST_TRY(br.prepare(&bv, 1, p, rb, b.status, o->generations, 0.0, st));
+    for (int g = 0; g < o->generations; ++g) {
+      ST_TRY(br.iteration(g, st));
+      CU_TRY(launch_pso_step(sw, b.fitness, st));
+    }
+  } else {
+    for (int g = 0; g < o->generations; ++g) {
+      ST_TRY(run_stencil(xr, rs, p, sw.x, P, b.u0, b.c0, rb, b.fitness, b.iters, nullptr,
+                         b.status, st));
+      CU_TRY(launch_pso_step(sw, b.fitness, st));
+    }
   }
   // Algorithm 1 step 11: final IFCM at the best personal best.
   CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));

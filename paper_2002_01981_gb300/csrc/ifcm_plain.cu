@@ -11,16 +11,110 @@ namespace {
 
 constexpr int PT = 256;   // threads per block of the plain kernel
 
+// Mean of u_kj over the in-volume voxels of the shell at Chebyshev distance r
+// around (X, Y, Z): the shell's H term where all its g_ik are 0 (reading R3).
+template <int C>
+__device__ __noinline__ void shell_mean(const float* __restrict__ u, int X, int Y, int Z, int r,
+                                        int nx, int ny, int nz, int pitch, float (&Hr)[C]) {
+  const size_t plane = static_cast<size_t>(nz) * ny * pitch;
+  float s[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) s[j] = 0.0f;
+  int n = 0;
+  for (int dz = -r; dz <= r; ++dz)
+    for (int dy = -r; dy <= r; ++dy) {
+      const bool face = (dz == -r || dz == r || dy == -r || dy == r);
+      for (int dx = -r; dx <= r; dx += face ? 1 : 2 * r) {
+        const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+        if (kx < 0 || kx >= nx || ky < 0 || ky >= ny || kz < 0 || kz >= nz) continue;
+        const size_t ko = (static_cast<size_t>(kz) * ny + ky) * pitch + kx;
+#pragma unroll
+        for (int j = 0; j < C; ++j) s[j] += u[j * plane + ko];
+        ++n;
+      }
+    }
+  const float inv = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) Hr[j] = s[j] * inv;
+}
+
+// H and F of Eqs 5 and 7 with V shells (reading R17: shell r is the surface
+// of the cube of Chebyshev radius r), weighted by W_r of Eq 10 and
+// renormalised over the shells that hold an in-volume voxel.
+template <int C>
+__device__ void shell_terms(const PlainArgs& a, const float* __restrict__ u, int X, int Y, int Z,
+                            float xc, float (&H)[C], float (&F)[C]) {
+  const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
+  float wsum = 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
+  for (int r = 1; r <= a.V; ++r) {
+    float hr[C], fr[C], G = 0.0f, Q = 0.0f;
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < C; ++j) hr[j] = fr[j] = 0.0f;
+    for (int dz = -r; dz <= r; ++dz)
+      for (int dy = -r; dy <= r; ++dy) {
+        const bool face = (dz == -r || dz == r || dy == -r || dy == r);
+        for (int dx = -r; dx <= r; dx += face ? 1 : 2 * r) {
+          const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+          if (kx < 0 || kx >= a.nx || ky < 0 || ky >= a.ny || kz < 0 || kz >= a.nz) continue;
+          const size_t ko = (static_cast<size_t>(kz) * a.ny + ky) * a.pitch + kx;
+          const float g = fabsf(xc - a.x[ko]);                                // Eq 6
+          const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);   // Eq 8
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const float uk = u ? u[j * plane + ko] : 1.0f / C;
+            hr[j] = fmaf(uk, g, hr[j]);
+            fr[j] = fmaf(uk * uk, q2, fr[j]);
+          }
+          G += g;
+          Q += q2;
+          ++n;
+        }
+      }
+    if (n == 0) continue;                      // empty shell: dropped
+    if (G > 0.0f) {
+      const float invG = __frcp_rn(G);
+#pragma unroll
+      for (int j = 0; j < C; ++j) hr[j] *= invG;
+    } else if (u) {
+      shell_mean<C>(u, X, Y, Z, r, a.nx, a.ny, a.nz, a.pitch, hr);
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) hr[j] = 1.0f / C;
+    }
+    const float invQ = __frcp_rn(Q), w = a.W[r - 1];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      H[j] = fmaf(w, hr[j], H[j]);
+      F[j] = fmaf(w, fr[j] * invQ, F[j]);
+    }
+    wsum += w;
+  }
+  if (wsum > 0.0f) {
+    const float inv = __frcp_rn(wsum);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      H[j] *= inv;
+      F[j] *= inv;
+    }
+  }
+}
+
 template <int C>
 __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
   __shared__ float s_red[PT / 32][2 * C + 2];
-  if (!a.active[0]) return;
+  const int pid = blockIdx.y;                  // particle of the launch
+  if (!a.active[pid]) return;
   const long long nvox = static_cast<long long>(a.nx) * a.ny * a.nz;
   const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
+  const float* u_src = a.u_src ? a.u_src + pid * a.src_pstride : nullptr;
+  float* u_dst = a.u_dst + pid * a.dst_pstride;
   MethodConsts k;
   if (a.lam_xi) {
-    k.lam = static_cast<float>(a.lam_xi[0]);
-    k.xi = static_cast<float>(a.lam_xi[1]);
+    k.lam = static_cast<float>(a.lam_xi[2 * pid]);
+    k.xi = static_cast<float>(a.lam_xi[2 * pid + 1]);
   } else {
     k.lam = a.lam;
     k.xi = a.xi;
@@ -31,7 +125,7 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
   k.m_is_2 = a.m_is_2;
   float cc[C];
 #pragma unroll
-  for (int j = 0; j < C; ++j) cc[j] = static_cast<float>(a.centres[j]);
+  for (int j = 0; j < C; ++j) cc[j] = static_cast<float>(a.centres[pid * C + j]);
   const bool stencil = a.stencil && (k.lam != 0.0f || k.xi != 0.0f);
 
   float s0[C], s1[C], Js = 0.0f, dm = 0.0f;
@@ -50,11 +144,13 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     const float xc = a.x[off];
     float uc[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) uc[j] = a.u_src ? a.u_src[j * plane + off] : 1.0f / C;
+    for (int j = 0; j < C; ++j) uc[j] = u_src ? u_src[j * plane + off] : 1.0f / C;
     float H[C], F[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
-    if (stencil) {
+    if (stencil && a.V > 1) {
+      shell_terms<C>(a, u_src, X, Y, Z, xc, H, F);
+    } else if (stencil) {
       float G = 0.0f, Q = 0.0f;
       int cnt = 0;
       for (int dz = -1; dz <= 1; ++dz)
@@ -68,7 +164,7 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
             const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);   // Eq 8
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-              const float uk = a.u_src ? a.u_src[j * plane + ko] : 1.0f / C;
+              const float uk = u_src ? u_src[j * plane + ko] : 1.0f / C;
               H[j] = fmaf(uk, g, H[j]);
               F[j] = fmaf(uk * uk, q2, F[j]);
             }
@@ -84,8 +180,8 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
           const float invG = __frcp_rn(G);
 #pragma unroll
           for (int j = 0; j < C; ++j) H[j] *= invG;
-        } else if (a.u_src) {
-          flat_neighbourhood_mean<C>(a.u_src, X, Y, Z, a.nx, a.ny, a.nz, a.pitch, H);
+        } else if (u_src) {
+          flat_neighbourhood_mean<C>(u_src, X, Y, Z, a.nx, a.ny, a.nz, a.pitch, H);
         } else {
 #pragma unroll
           for (int j = 0; j < C; ++j) H[j] = 1.0f / C;
@@ -96,7 +192,7 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     voxel_update<C>(H, F, xc, cc, k, u, um, Jv);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      a.u_dst[j * plane + off] = u[j];
+      u_dst[j * plane + off] = u[j];
       s0[j] += um[j];
       s1[j] = fmaf(um[j], xc, s1[j]);
       dm = fmaxf(dm, fabsf(u[j] - uc[j]));
@@ -121,16 +217,17 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     s_red[warp][2 * C + 1] = vm;
   }
   __syncthreads();
+  const size_t rec = static_cast<size_t>(pid) * a.n_rec + blockIdx.x;
   if (threadIdx.x < 2 * C + 1) {
     double sum = 0.0;
 #pragma unroll
     for (int w = 0; w < PT / 32; ++w) sum += static_cast<double>(s_red[w][threadIdx.x]);
-    a.partials[static_cast<size_t>(blockIdx.x) * (2 * C + 1) + threadIdx.x] = sum;
+    a.partials[rec * (2 * C + 1) + threadIdx.x] = sum;
   } else if (threadIdx.x == 2 * C + 1) {
     float mm = 0.0f;
 #pragma unroll
     for (int w = 0; w < PT / 32; ++w) mm = fmaxf(mm, s_red[w][2 * C + 1]);
-    a.dmax[blockIdx.x] = mm;
+    a.dmax[rec] = mm;
   }
 }
 
@@ -311,7 +408,9 @@ int plain_blocks(long long nvox, int vpt) {
 }
 
 cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s) {
-  PIFCM_DISPATCH_C(c, (plain_kernel<C><<<blocks, PT, 0, s>>>(a)); return cudaGetLastError());
+  if (a.P < 1 || a.V < 1 || a.V > kMaxV) return cudaErrorInvalidValue;
+  const dim3 grid(blocks, a.P);
+  PIFCM_DISPATCH_C(c, (plain_kernel<C><<<grid, PT, 0, s>>>(a)); return cudaGetLastError());
 }
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s) {

@@ -70,21 +70,32 @@ cudaError_t launch_stencil(int c, int np, bool bf16, const StencilArgs& a, int g
 long long bf16_unit_words(int c, int np, int P);
 
 // ------------------------------------- plain iteration (one thread per voxel)
+constexpr int kMaxV = 4;            // neighbourhood shells (Eq 10) of the plain kernel
+
+// Particle p of a launch is blockIdx.y: its U^t at u_src + p * src_pstride,
+// U^{t+1} at u_dst + p * dst_pstride, (lambda, xi) at lam_xi[2p], C^t at
+// centres[p c], records p * n_rec + blockIdx.x.
 struct PlainArgs {
   int nx, ny, nz, pitch;
   const float* x;
   const float* u_src;           // U^t, or NULL for u = 1/c
   float* u_dst;                 // U^{t+1}
-  const double* lam_xi;         // device (lambda, xi), or NULL: use lam / xi below
+  const double* lam_xi;         // device [P][2], or NULL: use lam / xi below
   float lam, xi;
-  const double* centres;        // [c] C^t
-  const int32_t* active;        // [1]
-  double* partials;             // [blocks][2c+1]
-  float* dmax;                  // [blocks]
+  const double* centres;        // [P][c] C^t
+  const int32_t* active;        // [P]
+  double* partials;             // [P][n_rec][2c+1]
+  float* dmax;                  // [P][n_rec]
   float dist_floor, m, inv_m1;
   int m_is_2;
   int vpt;                      // voxels per thread
   int stencil;                  // 0: lambda = xi = 0, no neighbourhood terms
+  int P;                        // particles (grid y)
+  long long src_pstride;        // elements between particles' U^t (0: one shared U^t)
+  long long dst_pstride;        // elements between particles' U^{t+1}
+  int n_rec;                    // records per particle (grid x)
+  int V;                        // shells, 1..kMaxV
+  float W[kMaxV];               // Eq 10 weights W_1..W_V
   DevStatus* status;
 };
 

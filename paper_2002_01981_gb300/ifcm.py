@@ -83,10 +83,14 @@ class Options:
     seed: int = 1
     init_max_iter: int = 300
     slice_z: int = -1
+    fitness: str = "restart"      # or "onestep" (Algorithm 2 steps 6-11 read literally)
 
     def native(self):
+        modes = {"restart": N.PIFCM_FITNESS_RESTART, "onestep": N.PIFCM_FITNESS_ONESTEP}
+        if self.fitness not in modes:
+            raise ValueError(f"fitness must be one of {sorted(modes)}")
         return N.PifcmOptions(self.P, self.generations, self.radius, self.vmax, self.seed,
-                              self.init_max_iter, self.slice_z)
+                              self.init_max_iter, self.slice_z, modes[self.fitness])
 
 
 def workspace(nbytes, device="cuda"):

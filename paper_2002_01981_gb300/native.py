@@ -37,10 +37,13 @@ class PsoState(Structure):
                 ("pbest_f", c_void_p), ("gen", c_void_p)]
 
 
+PIFCM_FITNESS_RESTART, PIFCM_FITNESS_ONESTEP = 0, 1
+
+
 class PifcmOptions(Structure):
     _fields_ = [("P", c_int32), ("generations", c_int32), ("radius", c_int32),
                 ("vmax", c_double), ("seed", c_uint64), ("init_max_iter", c_int32),
-                ("slice_z", c_int32)]
+                ("slice_z", c_int32), ("fitness_mode", c_int32)]
 
 
 class PifcmResult(Structure):

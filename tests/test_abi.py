@@ -42,7 +42,7 @@ def test_struct_sizes_match_the_header_layout():
     assert ctypes.sizeof(N.IfcmShape) == 16
     assert ctypes.sizeof(N.IfcmParams) == 64
     assert ctypes.sizeof(N.PsoState) == 64
-    assert ctypes.sizeof(N.PifcmOptions) == 40
+    assert ctypes.sizeof(N.PifcmOptions) == 48
     assert ctypes.sizeof(N.PifcmResult) == 8 * 8 + 4 * 8 + 8 + 4 * 4
 
 
@@ -72,7 +72,9 @@ def test_shape_validation(lib, shape, ok):
 
 
 @pytest.mark.parametrize("kw,status", [(dict(c=1), 1), (dict(c=9), 1), (dict(m=1.0), 1),
-                                       (dict(m=float("nan")), 1), (dict(V=2), 6),
+                                       (dict(m=float("nan")), 1), (dict(V=5), 6),
+                                       (dict(V=0), 6), (dict(V=2, h=0.0), 1),
+                                       (dict(V=2, u_dtype=1), 6),
                                        (dict(max_iter=0), 1), (dict(eps_u=-1.0), 1),
                                        (dict(dist_floor=0.0), 1), (dict(u_dtype=2), 1),
                                        (dict(u_dtype=-1), 1), (dict(reduce=2), 1)])
@@ -140,7 +142,8 @@ def test_options_validation(lib):
     p = _params()
     fake = ctypes.c_void_p(256)
     for o in (N.PifcmOptions(0, 3, 1, 0.2, 1, 300, -1), N.PifcmOptions(4, 0, 1, 0.2, 1, 300, -1),
-              N.PifcmOptions(4, 3, 1, 0.2, 1, 300, 8), N.PifcmOptions(4, 3, 1, -0.2, 1, 300, -1)):
+              N.PifcmOptions(4, 3, 1, 0.2, 1, 300, 8), N.PifcmOptions(4, 3, 1, -0.2, 1, 300, -1),
+              N.PifcmOptions(4, 3, 1, 0.2, 1, 300, -1, 2)):
         assert lib.pifcm3d(fake, shp, ctypes.byref(p), ctypes.byref(o), None, fake, fake,
                            1 << 40, None) == 1
 
