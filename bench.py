@@ -507,6 +507,44 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ GPU arm
+def run_small_kind(args):
+    """Small cases for profiler captures of the F2 / F3 kernels (a few GB on
+    the device): 'bf16' runs 3 iterations of 8 particles of the c = 6 256^3
+    workload with bf16 memberships; 'grad' runs ifcm_grad (K = 3) on the 128^3
+    differentiation workload."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_01981_gb300 import ifcm as G
+    from paper_2002_01981_gb300 import phantoms
+    dev = torch.device("cuda", 0)
+    if args.small_kind == "bf16":
+        raw = phantoms.multi_tissue(PREC_SHAPE, seed=5, sigma=0.1)
+        nx = PREC_SHAPE[2]
+        x = G.ifcm_normalize(torch.from_numpy(phantoms.pad_pitch(raw)).to(dev), nx=nx)
+        U0, C0, _, _ = G.ifcm_fit(x, G.Params(c=PREC_C, max_iter=20, eps_u=EPS), (0.0, 0.0),
+                                  nx=nx)
+        lam = G.Swarm(8, seed=5).init().x
+        prm = G.Params(c=PREC_C, m=M, max_iter=3, eps_u=0.0, u_dtype="bf16")
+        for _ in range(args.steps):
+            fit, _, _ = G.pso_fitness_batch(x, prm, lam, U0, C0, nx=nx)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_kind": "bf16", "fitness": fit.cpu().numpy().tolist()}))
+    else:
+        raw = phantoms.gaussian_phantom(DIFF_SHAPE, seed=4, sigma=0.09)
+        nx = DIFF_SHAPE[2]
+        x = G.ifcm_normalize(torch.from_numpy(phantoms.pad_pitch(raw)).to(dev), nx=nx)
+        U0, C0, _, _ = G.ifcm_fit(x, G.Params(c=DIFF_C, max_iter=20, eps_u=EPS), (0.0, 0.0),
+                                  nx=nx)
+        prm = G.Params(c=DIFF_C, m=M)
+        for _ in range(args.steps):
+            J, g = G.ifcm_grad(x, prm, (0.3, 0.2), U0, C0, 3, nx=nx)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_kind": "grad", "J": float(J), "grad": g.cpu().numpy().tolist()}))
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -673,9 +711,13 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same volume and particles, 1 generation x "
                          "3 iterations")
+    ap.add_argument("--small-kind", choices=("bf16", "grad"), default=None,
+                    help="profiling case of the bf16 stencil or of the adjoint kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.small_kind:
+        return run_small_kind(args)
     return run_ours(args)
 
 
