@@ -233,7 +233,10 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
  * share each stencil launch (up to 64 volumes and 4096 particles per launch).
  * Volumes are taken in order, grouped by c, and packed into waves that fit
  * ws_bytes; a wave runs to completion before the next reuses the workspace.
- * Results are identical to pso_fitness_batch on each volume alone.
+ * Each particle computes the same IFCM run as in pso_fitness_batch on its
+ * volume alone; results agree to the order of the partial sums, which
+ * depends on how the launch cuts the volume into work items (z-chunks,
+ * particles or clusters per packed lane) and so on the whole batch.
  * vols: HOST array of n descriptors (pointers inside are device memory).
  * p: m, max_iter, eps_u, dist_floor and V are shared; p->c is ignored.
  */

@@ -78,6 +78,16 @@ ifcm_status check_params(const ifcm_params* p) {
 
 bool is_bf16(const ifcm_params* p) { return p->u_dtype == IFCM_U_BF16; }
 
+// Layout of the memberships between iterations for a batch of P_total
+// particles: bf16 pair words when asked for; FP32 planes for one-particle runs
+// (their workspace stays c planes per buffer) and for V > 1 shells (the plain
+// kernel); float2 pair words for every other FP32 batch.
+int run_layout(const ifcm_params* p, int P_total) {
+  if (is_bf16(p)) return UL_BF16;
+  if (p->V > 1 || P_total < 2) return UL_PLANAR;
+  return UL_F32P;
+}
+
 // The kernels index one particle's c membership planes with 32-bit offsets.
 ifcm_status check_extent(const ifcm_shape& s, const ifcm_params* p) {
   const double elems = static_cast<double>(p->c) * s.pitch_x * s.ny * s.nz;
@@ -144,12 +154,12 @@ constexpr int kPlainVpt = 32;
 // buffers per volume (P particles each), the partial records of every
 // particle's tiles, and the per-particle run state (particle p of volume v is
 // state index pbase[v] + p).
-// With bf16 memberships ua / ub hold pair words for either plan (np = 1 or
-// 2, whichever is larger) and u0p the packed shared start; np is the plan
-// the last run used (it fixes the word layout).
+// With a pair-word layout ua / ub hold words for either plan (np = 1 or 2,
+// whichever is larger) and u0p the packed shared start; np is the plan the
+// last run used (it fixes the word layout).
 struct RunBufs {
   int n;
-  bool bf16;
+  int layout;
   int np;
   float* ua[kMaxVols];
   float* ub[kMaxVols];
@@ -163,27 +173,29 @@ struct RunBufs {
 };
 
 // 4-byte elements per voxel of one membership buffer of P particles.
-size_t run_buffer_elems(int c, int P, bool bf16) {
-  if (!bf16) return static_cast<size_t>(P) * c;
-  long long w = bf16_unit_words(c, 1, P);
-  if (c <= 4 && bf16_unit_words(c, 2, P) > w) w = bf16_unit_words(c, 2, P);
-  // the FCM start (FP32, one particle) also runs in these buffers
+size_t run_buffer_elems(int c, int P, int layout) {
+  if (layout == UL_PLANAR) return static_cast<size_t>(P) * c;
+  long long w = pair_unit_words(c, 1, P);
+  if (c <= 4 && pair_unit_words(c, 2, P) > w) w = pair_unit_words(c, 2, P);
+  if (layout == UL_F32P) w *= 2;          // 8-byte words
+  // the FCM start (FP32 planes, one particle) also runs in these buffers
   if (w < c) w = c;
   return static_cast<size_t>(w);
 }
 
 RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, int c,
-                   bool bf16) {
+                   int layout) {
   RunBufs r{};
   r.n = n;
-  r.bf16 = bf16;
+  r.layout = layout;
   long long recs = 0;
   int pb = 0;
   for (int v = 0; v < n; ++v) {
     const size_t pl = plane_elems(shapes[v]);
-    r.ua[v] = cv.take<float>(run_buffer_elems(c, P[v], bf16) * pl);
-    r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], bf16) * pl);
-    r.u0p[v] = bf16 ? cv.take<float>(static_cast<size_t>(c) * pl) : nullptr;
+    r.ua[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
+    r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
+    r.u0p[v] = layout == UL_PLANAR ? nullptr
+               : cv.take<float>(static_cast<size_t>(c) * pl * (layout == UL_F32P ? 2 : 1));
     const long long nvox = static_cast<long long>(shapes[v].nx) * shapes[v].ny * shapes[v].nz;
     int nrec = max_tiles(shapes[v]);
     const int nplain = plain_blocks(nvox, kPlainVpt);      // the plain kernel's records (P = 1)
@@ -204,8 +216,8 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
   return r;
 }
 
-RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P, bool bf16) {
-  return carve_runs(cv, &s, &P, 1, c, bf16);
+RunBufs carve_run(Carver& cv, const ifcm_shape& s, int c, int P, int layout) {
+  return carve_runs(cv, &s, &P, 1, c, layout);
 }
 
 RunState shifted(const RunState& st, int pbase, int c) {
@@ -256,10 +268,12 @@ ifcm_status get_encode() {
 // Box of one stencil plane: TX + 8 columns (4-voxel aligned margins) by TY + 2 rows.
 constexpr cuuint32_t kBoxX = kTX + 8, kBoxY = kTY + 2;
 
+// planes <= 0: the volume x; else a membership map of `planes` planes of
+// elem_bytes-byte elements (4: FP32 or a bf16x2 word; 8: a float2 word).
 ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int planes,
-                     int box_planes) {
+                     int box_planes, int elem_bytes = 4) {
   ST_TRY(get_encode());
-  const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * 4;
+  const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * (planes <= 0 ? 4 : elem_bytes);
   if (planes <= 0) {   // 3D volume map: positions outside the volume read as NaN
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
                           static_cast<cuuint64_t>(s.nz)};
@@ -278,7 +292,9 @@ ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int
   cuuint64_t strides[3] = {row, row * s.ny, row * s.ny * s.nz};
   cuuint32_t box[4] = {kBoxX, kBoxY, 1, static_cast<cuuint32_t>(box_planes)};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+  CUresult r = g_encode(m, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        4, const_cast<float*>(base), dims,
                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -362,8 +378,8 @@ long long plan_items(const BatchVol* vols, int n, const StencilPlan& pl) {
   return items;
 }
 
-int plan_grid(int c, bool bf16, const StencilPlan& pl, long long items) {
-  long long g = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np, bf16);
+int plan_grid(int c, int layout, const StencilPlan& pl, long long items) {
+  long long g = static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np, layout);
   if (g > items) g = items;
   return g < 1 ? 1 : static_cast<int>(g);
 }
@@ -378,9 +394,13 @@ int most_chunks(const BatchVol* vols, int n) {
 // Built-in choice: the deepest chunks that still give every CTA of the
 // persistent grid at least four items (whole columns when the batch is big
 // enough: fewer halo planes and pipeline fills per voxel).
-StencilPlan heuristic_plan(const BatchVol* vols, int n, int c, bool bf16) {
-  StencilPlan pl{stencil_default_np(c), 1};
-  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np, bf16);
+StencilPlan heuristic_plan(const BatchVol* vols, int n, int c, int layout) {
+  int P_total = 0;
+  for (int v = 0; v < n; ++v) P_total += vols[v].P;
+  // one particle: its clusters in pairs (two particles per item would
+  // compute a duplicate lane)
+  StencilPlan pl{P_total == 1 ? 1 : stencil_default_np(c), 1};
+  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np, layout);
   const int kmax = most_chunks(vols, n);
   while (pl.chunks < kmax && plan_items(vols, n, pl) < want) ++pl.chunks;
   return pl;
@@ -437,16 +457,17 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.lam_xi = bv.lam_xi;
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
     ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
-    if (rb.bf16) {
+    if (rb.layout != UL_PLANAR) {
       // pair words: K planes per unit (a particle pair for np = 2, a particle
       // for np = 1); iteration 0 reads the packed shared start (one unit)
       const int K = pl.np == 2 ? c : (c + 1) / 2;
       const int units = pl.np == 2 ? (bv.P + 1) / 2 : bv.P;
+      const int wb = rb.layout == UL_F32P ? 8 : 4;
       const float* src = kind == 0 ? rb.u0p[v] : (kind == 1 ? rb.ua[v] : rb.ub[v]);
       d.u_src = src;
-      d.src_pstride = kind == 0 ? 0 : static_cast<long long>(K) * plane;
+      d.src_pstride = kind == 0 ? 0 : static_cast<long long>(K) * plane;   // in words
       d.src_cstride = kind == 0 ? 0 : K;
-      ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? K : units * K, K));
+      ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? K : units * K, K, wb));
     } else {
       const float* src = kind == 0 ? bv.u0 : (kind == 1 ? rb.ua[v] : rb.ub[v]);
       d.u_src = src;
@@ -458,12 +479,12 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
   return IFCM_OK;
 }
 
-// bf16 runs: each volume's shared start as pair words laid out for np.
+// Pair-word runs: each volume's shared start as pair words laid out for np.
 ifcm_status pack_starts(const BatchVol* vols, int n, int c, const RunBufs& rb, int np,
                         cudaStream_t st) {
-  if (!rb.bf16) return IFCM_OK;
+  if (rb.layout == UL_PLANAR) return IFCM_OK;
   for (int v = 0; v < n; ++v)
-    CU_TRY(launch_pack_start(vols[v].u0, reinterpret_cast<uint32_t*>(rb.u0p[v]), c, np,
+    CU_TRY(launch_pack_start(vols[v].u0, rb.u0p[v], c, np, rb.layout,
                              static_cast<long long>(plane_elems(vols[v].shape)), st));
   return IFCM_OK;
 }
@@ -475,8 +496,8 @@ ifcm_status pack_starts(const BatchVol* vols, int n, int c, const RunBufs& rb, i
 ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
                       DevStatus* status, cudaStream_t st, StencilPlan* best) {
   const int c = p->c;
-  const bool bf = is_bf16(p);
-  const StencilPlan h = heuristic_plan(vols, n, c, bf);
+  const int lay = rb.layout;
+  const StencilPlan h = heuristic_plan(vols, n, c, lay);
   const int kmax = most_chunks(vols, n);
   std::vector<StencilPlan> cand;
   for (int np = 1; np <= 2; ++np) {
@@ -500,13 +521,13 @@ ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const R
     rc = build_args(args[0], vols, n, p, rb, pl, 0, status);
     if (rc == IFCM_OK) rc = build_args(args[1], vols, n, p, rb, pl, 1, status);
     if (rc != IFCM_OK) break;
-    const int grid = plan_grid(c, bf, pl, plan_items(vols, n, pl));
+    const int grid = plan_grid(c, lay, pl, plan_items(vols, n, pl));
     rc = pack_starts(vols, n, c, rb, pl.np, st);
     if (rc != IFCM_OK) break;
-    cudaError_t e = launch_stencil(c, pl.np, bf, args[0], grid, st);
+    cudaError_t e = launch_stencil(c, pl.np, lay, args[0], grid, st);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int r = 0; r < 2 && e == cudaSuccess; ++r)
-      e = launch_stencil(c, pl.np, bf, args[1], grid, st);
+      e = launch_stencil(c, pl.np, lay, args[1], grid, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -545,7 +566,7 @@ ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU_TRY(cudaStreamIsCapturing(st, &cap));
   if (mode == 0 || cap != cudaStreamCaptureStatusNone) {
-    *out = heuristic_plan(vols, n, p->c, is_bf16(p));   // a captured stream is never timed
+    *out = heuristic_plan(vols, n, p->c, rb.layout);   // a captured stream is never timed
     return IFCM_OK;
   }
   ST_TRY(tune_plan(vols, n, p, rb, status, st, out));
@@ -554,7 +575,7 @@ ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const
   return IFCM_OK;
 }
 
-void fill_plain_method(PlainArgs& a, const ifcm_params* p);
+void fill_plain_method(PlainArgs& a, ShellArgs& sh, const ifcm_params* p);
 
 // A prepared batch of IFCM runs of every particle of n volumes (same c,
 // n <= kMaxVols): run state initialised from each volume's c0, the launch
@@ -595,7 +616,7 @@ struct BatchRun {
       ST_TRY(pack_starts(vols, n, c, *rb, pl.np, st));
       args.resize(3);
       for (int k = 0; k < 3; ++k) ST_TRY(build_args(args[k], vols, n, p, *rb, pl, k, status));
-      grid = plan_grid(c, rb->bf16, pl, plan_items(vols, n, pl));
+      grid = plan_grid(c, rb->layout, pl, plan_items(vols, n, pl));
     } else {
       rb->np = 1;
     }
@@ -630,7 +651,7 @@ struct BatchRun {
     if (!wide) {
       cudaEvent_t ev_end = nullptr;
       cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-      CU_TRY(launch_stencil(c, pl.np, rb->bf16, args[kind], grid, st));
+      CU_TRY(launch_stencil(c, pl.np, rb->layout, args[kind], grid, st));
       if (ev_beg) cudaEventRecord(ev_end, st);
     } else {
       for (int v = 0; v < n; ++v) {
@@ -644,21 +665,22 @@ struct BatchRun {
         a.nz = s.nz;
         a.pitch = s.pitch_x;
         a.x = bv.x;
+        ShellArgs sh;
+        fill_plain_method(a, sh, p);
         a.u_src = kind == 0 ? bv.u0 : (kind == 1 ? rb->ua[v] : rb->ub[v]);
-        a.src_pstride = kind == 0 ? 0 : c * plane;
+        sh.src_pstride = kind == 0 ? 0 : c * plane;
         a.u_dst = kind == 1 ? rb->ub[v] : rb->ua[v];
-        a.dst_pstride = c * plane;
+        sh.dst_pstride = c * plane;
         a.lam_xi = bv.lam_xi;
         a.centres = rb->st.centres + static_cast<size_t>(rb->pbase[v]) * c;
         a.active = rb->st.active + rb->pbase[v];
         a.partials = rb->partials + static_cast<size_t>(rb->rec_base[v]) * (2 * c + 1);
         a.dmax = rb->dmax + rb->rec_base[v];
-        fill_plain_method(a, p);
         a.stencil = 1;
-        a.P = bv.P;
-        a.n_rec = blocks;
+        sh.P = bv.P;
+        sh.n_rec = blocks;
         a.status = status;
-        CU_TRY(launch_plain(c, a, blocks, st));
+        CU_TRY(launch_plain(c, a, sh, blocks, st));
       }
     }
     CU_TRY(launch_reduce(c, r, st));
@@ -685,25 +707,27 @@ ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* 
   return run_stencil_batch(&bv, 1, p, rb, status, st);
 }
 
-// Method constants and Eq 10 weights of a plain-kernel launch.
-void fill_plain_method(PlainArgs& a, const ifcm_params* p) {
+// Method constants of a plain-kernel launch, and the shells with their Eq 10
+// weights (one particle unless the caller sets more).
+void fill_plain_method(PlainArgs& a, ShellArgs& sh, const ifcm_params* p) {
   a.dist_floor = static_cast<float>(p->dist_floor);
   a.m = static_cast<float>(p->m);
   a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
   a.m_is_2 = p->m == 2.0;
   a.vpt = kPlainVpt;
-  a.V = p->V;
+  sh = ShellArgs{};
+  sh.P = 1;
+  sh.V = p->V;
   double e[kMaxV], sum = 0.0;
   for (int r = 1; r <= p->V; ++r) sum += (e[r - 1] = std::exp(-r / (p->V > 1 ? p->h : 1.0)));
-  for (int r = 1; r <= p->V; ++r) a.W[r - 1] = static_cast<float>(e[r - 1] / sum);
+  for (int r = 1; r <= p->V; ++r) sh.W[r - 1] = static_cast<float>(e[r - 1] / sum);
 }
 
 // Particle 0's final memberships (P = 1 runs) as FP32 [c][plane].
 ifcm_status copy_out(const RunBufs& rb, int c, size_t plane, float* u_out, cudaStream_t st) {
-  if (rb.bf16)
-    CU_TRY(launch_unpack_select(reinterpret_cast<const uint32_t*>(rb.ua[0]),
-                                reinterpret_cast<const uint32_t*>(rb.ub[0]), rb.st.iters, u_out,
-                                c, rb.np, static_cast<long long>(plane), st));
+  if (rb.layout != UL_PLANAR)
+    CU_TRY(launch_unpack_select(rb.ua[0], rb.ub[0], rb.st.iters, u_out, c, rb.np, rb.layout,
+                                static_cast<long long>(plane), st));
   else
     CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, u_out,
                               static_cast<long long>(c) * plane, st));
@@ -734,10 +758,10 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   a.active = rb.st.active;
   a.partials = rb.partials;
   a.dmax = rb.dmax;
-  fill_plain_method(a, p);
+  ShellArgs sh;
+  fill_plain_method(a, sh, p);
+  sh.n_rec = blocks;
   a.stencil = stencil ? 1 : 0;
-  a.P = 1;
-  a.n_rec = blocks;
   a.status = status;
   ReduceArgs r{};
   r.n_vol = 1;
@@ -759,7 +783,7 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   for (int it = 0; it < max_iter; ++it) {
     a.u_dst = (it % 2 == 0) ? rb.ua[0] : rb.ub[0];
     a.u_src = it == 0 ? u_init : ((it % 2 == 1) ? rb.ua[0] : rb.ub[0]);
-    CU_TRY(launch_plain(c, a, blocks, st));
+    CU_TRY(launch_plain(c, a, sh, blocks, st));
     CU_TRY(launch_reduce(c, r, st));
     if (host_check) {
       int32_t act = 0;
@@ -827,7 +851,7 @@ PifcmBufs carve_pifcm(Carver& cv, const ifcm_shape& s, const ifcm_params* p,
   b.J_init = cv.take<double>(1);
   b.updates = cv.take<unsigned long long>(1);
   b.norm = carve_norm(cv, s);
-  b.run = carve_run(cv, rs, c, P, is_bf16(p));
+  b.run = carve_run(cv, rs, c, P, run_layout(p, P));
   return b;
 }
 
@@ -923,7 +947,7 @@ size_t ifcm_fit_workspace_bytes(ifcm_shape shape, const ifcm_params* p) {
   Carver cv(nullptr);
   carve_status(cv);
   cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));   // uniform start
-  carve_run(cv, shape, p->c, 1, is_bf16(p));
+  carve_run(cv, shape, p->c, 1, run_layout(p, 1));
   return cv.off + 256;
 }
 
@@ -945,7 +969,7 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
   float* uni = cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
-  RunBufs rb = carve_run(cv, shape, p->c, 1, is_bf16(p));
+  RunBufs rb = carve_run(cv, shape, p->c, 1, run_layout(p, 1));
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   const float* start = u_init;
@@ -977,7 +1001,7 @@ ifcm_status ifcm_fit_plain(const float* x, ifcm_shape shape, const ifcm_params* 
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
   cv.take<float>(static_cast<size_t>(p->c) * plane_elems(shape));
-  RunBufs rb = carve_run(cv, shape, p->c, 1, false);
+  RunBufs rb = carve_run(cv, shape, p->c, 1, UL_PLANAR);
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   ST_TRY(run_plain(x, shape, p, nullptr, static_cast<float>(lambda), static_cast<float>(xi),
@@ -994,7 +1018,7 @@ size_t pso_fitness_batch_workspace_bytes(ifcm_shape shape, const ifcm_params* p,
   if (!p || p->c < 2 || p->c > kMaxC || P < 1) return 0;
   Carver cv(nullptr);
   carve_status(cv);
-  carve_run(cv, shape, p->c, P, is_bf16(p));
+  carve_run(cv, shape, p->c, P, run_layout(p, P));
   return cv.off + 256;
 }
 
@@ -1016,7 +1040,7 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver cv(ws);
   DevStatus* status = carve_status(cv);
-  RunBufs rb = carve_run(cv, shape, p->c, P, is_bf16(p));
+  RunBufs rb = carve_run(cv, shape, p->c, P, run_layout(p, P));
   CU_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
   return run_stencil(x, shape, p, lam_xi, P, u0, c0, rb, fitness, iters, c_out, status, st);
@@ -1055,7 +1079,7 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
   BatchVol bv{};
   bv.shape = shape;
   bv.P = P;
-  StencilPlan pl = heuristic_plan(&bv, 1, c, false);
+  StencilPlan pl = heuristic_plan(&bv, 1, c, P >= 2 ? UL_F32P : UL_PLANAR);
   int32_t tuned = 0;
   {
     std::lock_guard<std::mutex> lk(g_tune.mu);
@@ -1077,7 +1101,11 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
 // -------------------------------------------------- pso_fitness_multi
 namespace {
 
-size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c, bool bf16) {
+// Multi-volume batches: the layout depends on the parameters only (a wave's
+// particle count changes while waves are packed).
+int multi_layout(const ifcm_params* p) { return run_layout(p, 2); }
+
+size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c, int layout) {
   ifcm_shape shapes[kMaxVols];
   int P[kMaxVols];
   for (int i = 0; i < n; ++i) {
@@ -1086,7 +1114,7 @@ size_t wave_bytes(const ifcm_batch_volume* vols, const int* idx, int n, int c, b
   }
   Carver cv(nullptr);
   carve_status(cv);
-  carve_runs(cv, shapes, P, n, c, bf16);
+  carve_runs(cv, shapes, P, n, c, layout);
   return cv.off + 256;
 }
 
@@ -1113,11 +1141,11 @@ ifcm_status check_multi(const ifcm_batch_volume* vols, int32_t n, const ifcm_par
 // Volumes in the wave that starts at g[b]: as many as fit one launch
 // (kMaxVols volumes, kMaxBatchParticles particles) and ws_bytes.
 int wave_size(const ifcm_batch_volume* vols, const std::vector<int>& g, size_t b, int c,
-              bool bf16, size_t ws_bytes) {
+              int layout, size_t ws_bytes) {
   int cnt = 0, parts = 0;
   while (b + cnt < g.size() && cnt < kMaxVols &&
          parts + vols[g[b + cnt]].P <= kMaxBatchParticles &&
-         wave_bytes(vols, g.data() + b, cnt + 1, c, bf16) <= ws_bytes)
+         wave_bytes(vols, g.data() + b, cnt + 1, c, layout) <= ws_bytes)
     parts += vols[g[b + cnt++]].P;
   return cnt;
 }
@@ -1142,8 +1170,8 @@ size_t pso_fitness_multi_workspace_bytes(const ifcm_batch_volume* vols, int32_t 
     const std::vector<int> g = group_of(vols, n, c);
     // whole group, in launch-sized pieces
     for (size_t b = 0; b < g.size();) {
-      const int cnt = wave_size(vols, g, b, c, is_bf16(p), static_cast<size_t>(-1));
-      const size_t w = wave_bytes(vols, g.data() + b, cnt, c, is_bf16(p));
+      const int cnt = wave_size(vols, g, b, c, multi_layout(p), static_cast<size_t>(-1));
+      const size_t w = wave_bytes(vols, g.data() + b, cnt, c, multi_layout(p));
       if (w > need) need = w;
       b += cnt;
     }
@@ -1156,7 +1184,7 @@ size_t pso_fitness_multi_min_workspace_bytes(const ifcm_batch_volume* vols, int3
   if (check_multi(vols, n, p) != IFCM_OK) return 0;
   size_t need = 0;
   for (int i = 0; i < n; ++i) {
-    const size_t w = wave_bytes(vols, &i, 1, vols[i].c, is_bf16(p));
+    const size_t w = wave_bytes(vols, &i, 1, vols[i].c, multi_layout(p));
     if (w > need) need = w;
   }
   return need;
@@ -1169,7 +1197,8 @@ int32_t pso_fitness_multi_waves(const ifcm_batch_volume* vols, int32_t n, const 
   int32_t waves = 0;
   for (int c = 2; c <= kMaxC; ++c) {
     const std::vector<int> g = group_of(vols, n, c);
-    for (size_t b = 0; b < g.size(); ++waves) b += wave_size(vols, g, b, c, is_bf16(p), ws_bytes);
+    for (size_t b = 0; b < g.size(); ++waves)
+      b += wave_size(vols, g, b, c, multi_layout(p), ws_bytes);
   }
   return waves;
 }
@@ -1194,7 +1223,7 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
     ifcm_params pc = *p;
     pc.c = c;
     for (size_t b = 0; b < g.size();) {
-      const int cnt = wave_size(vols, g, b, c, is_bf16(p), ws_bytes);
+      const int cnt = wave_size(vols, g, b, c, multi_layout(p), ws_bytes);
       std::vector<BatchVol> bv(cnt);
       ifcm_shape shapes[kMaxVols];
       int P[kMaxVols];
@@ -1206,7 +1235,7 @@ ifcm_status pso_fitness_multi(const ifcm_batch_volume* vols, int32_t n, const if
       }
       Carver cv(ws);
       DevStatus* status = carve_status(cv);
-      RunBufs rb = carve_runs(cv, shapes, P, cnt, c, is_bf16(p));
+      RunBufs rb = carve_runs(cv, shapes, P, cnt, c, multi_layout(p));
       CU_TRY(cudaMemsetAsync(rb.st.updates, 0, sizeof(unsigned long long), st));
       ST_TRY(run_stencil_batch(bv.data(), cnt, &pc, rb, status, st));
       b += cnt;
@@ -1458,7 +1487,7 @@ StencilPlan peek_plan(const BatchVol* vols, int n, const ifcm_params* p) {
   if (g_tune.force.np > 0 && stencil_np_supported(p->c, g_tune.force.np)) return g_tune.force;
   auto it = g_tune.cache.find(plan_key(vols, n, p->c, p->u_dtype));
   if (it != g_tune.cache.end()) return it->second;
-  return heuristic_plan(vols, n, p->c, is_bf16(p));
+  return heuristic_plan(vols, n, p->c, is_bf16(p) ? UL_BF16 : UL_PLANAR);
 }
 
 // Scratch of a gradient evaluation: the run state of one particle, the
@@ -1485,7 +1514,7 @@ GradBufs carve_grad(Carver& cv, const ifcm_shape& s, int c, int K) {
   const size_t pl = plane_elems(s);
   const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
   g.status = carve_status(cv);
-  g.run = carve_run(cv, s, c, 1, false);
+  g.run = carve_run(cv, s, c, 1, UL_PLANAR);
   g.ckpt = cv.take<float>(static_cast<size_t>(K) * c * pl);
   g.trace = cv.take<double>(static_cast<size_t>(K) * (2 * c + 1));
   g.A = cv.take<float>(static_cast<size_t>(c) * pl);
@@ -1533,14 +1562,14 @@ ifcm_status grad_forward(const float* x, const ifcm_shape& s, const ifcm_params*
   r.vol[0].fitness = J_out;
   r.vol[0].trace = g.trace;
   std::vector<StencilArgs> args(1);
-  const int grid = plan_grid(c, false, plan, plan_items(&bv, 1, plan));
+  const int grid = plan_grid(c, rb.layout, plan, plan_items(&bv, 1, plan));
   for (int t = 0; t < K; ++t) {
     bv.u0 = t == 0 ? u0 : g.ckpt + static_cast<size_t>(t - 1) * c * pl;
     rb.ua[0] = g.ckpt + static_cast<size_t>(t) * c * pl;
     ST_TRY(build_args(args[0], &bv, 1, &pk, rb, plan, 0, g.status));
     cudaEvent_t ev_end = nullptr;
     cudaEvent_t ev_beg = prof_begin(st, &ev_end);
-    CU_TRY(launch_stencil(c, plan.np, false, args[0], grid, st));
+    CU_TRY(launch_stencil(c, plan.np, rb.layout, args[0], grid, st));
     if (ev_beg) cudaEventRecord(ev_end, st);
     CU_TRY(launch_reduce(c, r, st));
   }

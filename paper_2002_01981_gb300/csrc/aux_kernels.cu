@@ -108,9 +108,21 @@ __device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
 
 // Shared start as pair words: np = 2 -> word plane j = (u_j, u_j) (both
 // particles of every pair start from it); np = 1 -> word plane k =
-// (u_2k, u_2k+1), with 0 in the high half past the last cluster.
-__global__ void pack_start_kernel(const float* u0, uint32_t* out, int c, int np,
-                                  long long plane) {
+// (u_2k, u_2k+1), with 0 in the high half past the last cluster.  W is a
+// bf16x2 word (uint32_t) or a float2 word.
+__device__ __forceinline__ void put_pair(uint32_t* out, long long i, float lo, float hi) {
+  out[i] = bf16_pair(lo, hi);
+}
+__device__ __forceinline__ void put_pair(float2* out, long long i, float lo, float hi) {
+  out[i] = make_float2(lo, hi);
+}
+__device__ __forceinline__ float lane_of(uint32_t w, bool hi) {
+  return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+}
+__device__ __forceinline__ float lane_of(float2 w, bool hi) { return hi ? w.y : w.x; }
+
+template <class W>
+__global__ void pack_start_kernel(const float* u0, W* out, int c, int np, long long plane) {
   const int planes = np == 2 ? c : (c + 1) / 2;
   const long long n = static_cast<long long>(planes) * plane;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
@@ -118,27 +130,26 @@ __global__ void pack_start_kernel(const float* u0, uint32_t* out, int c, int np,
     const long long k = i / plane, v = i - k * plane;
     if (np == 2) {
       const float u = u0[k * plane + v];
-      out[i] = bf16_pair(u, u);
+      put_pair(out, i, u, u);
     } else {
       const float lo = u0[(2 * k) * plane + v];
       const float hi = 2 * k + 1 < c ? u0[(2 * k + 1) * plane + v] : 0.0f;
-      out[i] = bf16_pair(lo, hi);
+      put_pair(out, i, lo, hi);
     }
   }
 }
 
 // Particle 0's memberships (unit 0, low lane for np = 2) as FP32 planes.
-__global__ void unpack_select_kernel(const uint32_t* a, const uint32_t* b,
-                                     const int32_t* iters, float* dst, int c, int np,
-                                     long long plane) {
-  const uint32_t* src = ((*iters) & 1) ? a : b;
+template <class W>
+__global__ void unpack_select_kernel(const W* a, const W* b, const int32_t* iters, float* dst,
+                                     int c, int np, long long plane) {
+  const W* src = ((*iters) & 1) ? a : b;
   const long long n = static_cast<long long>(c) * plane;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long j = i / plane, v = i - j * plane;
-    const uint32_t w = np == 2 ? src[j * plane + v] : src[(j >> 1) * plane + v];
-    const bool hi = np == 2 ? false : (j & 1);
-    dst[i] = __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+    const W w = np == 2 ? src[j * plane + v] : src[(j >> 1) * plane + v];
+    dst[i] = lane_of(w, np == 2 ? false : (j & 1));
   }
 }
 
@@ -302,23 +313,34 @@ cudaError_t launch_select_copy(const float* a, const float* b, const int32_t* it
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_start(const float* u0, uint32_t* out, int c, int np, long long plane,
-                              cudaStream_t s) {
+cudaError_t launch_pack_start(const float* u0, void* out, int c, int np, int layout,
+                              long long plane, cudaStream_t s) {
   const long long n = static_cast<long long>(np == 2 ? c : (c + 1) / 2) * plane;
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  pack_start_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(u0, out, c, np, plane);
+  if (layout == UL_BF16)
+    pack_start_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
+        u0, static_cast<uint32_t*>(out), c, np, plane);
+  else
+    pack_start_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
+        u0, static_cast<float2*>(out), c, np, plane);
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_select(const uint32_t* a, const uint32_t* b, const int32_t* iters,
-                                 float* dst, int c, int np, long long plane, cudaStream_t s) {
+cudaError_t launch_unpack_select(const void* a, const void* b, const int32_t* iters, float* dst,
+                                 int c, int np, int layout, long long plane, cudaStream_t s) {
   const long long n = static_cast<long long>(c) * plane;
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  unpack_select_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(a, b, iters, dst, c, np, plane);
+  if (layout == UL_BF16)
+    unpack_select_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
+        static_cast<const uint32_t*>(a), static_cast<const uint32_t*>(b), iters, dst, c, np,
+        plane);
+  else
+    unpack_select_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
+        static_cast<const float2*>(a), static_cast<const float2*>(b), iters, dst, c, np, plane);
   return cudaGetLastError();
 }
 

@@ -200,6 +200,38 @@ __device__ __noinline__ void flat_neighbourhood_mean_bf16(const uint32_t* __rest
   for (int j = 0; j < C; ++j) H[j] = s[j] * inv;
 }
 
+// The same mean over float2 pair words (pairing as for the bf16 words above).
+template <int C>
+__device__ __noinline__ void flat_neighbourhood_mean_f32p(const float2* __restrict__ u,
+                                                          bool pair_particles, int lane, int X,
+                                                          int Y, int Z, int nx, int ny, int nz,
+                                                          int pitch, float (&H)[C]) {
+  const size_t plane = static_cast<size_t>(nz) * ny * pitch;
+  float s[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) s[j] = 0.0f;
+  int n = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+        if (kx < 0 || kx >= nx || ky < 0 || ky >= ny || kz < 0 || kz >= nz) continue;
+        const size_t off = (static_cast<size_t>(kz) * ny + ky) * pitch + kx;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const int wp = pair_particles ? j : j >> 1;
+          const int hi = pair_particles ? lane : (j & 1);
+          const float2 w = u[wp * plane + off];
+          s[j] += hi ? w.y : w.x;
+        }
+        ++n;
+      }
+  const float inv = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) H[j] = s[j] * inv;
+}
+
 // Compensated (Neumaier) FP32 summation step: sum + comp carries the running
 // total with the rounding error of every addition kept in comp.
 __device__ __forceinline__ void neumaier_add(float& sum, float& comp, float v) {

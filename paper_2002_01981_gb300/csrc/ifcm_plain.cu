@@ -1,7 +1,8 @@
-// The plain IFCM iteration (one thread per voxel, neighbours read straight
-// from global memory: the shape of the paper's Algorithm 2 steps 6-8), the
-// per-particle reduction that finalises every iteration (Eq 3 centres, Eq 1
-// objective, stop rule), and the run-state initialisation.
+// The plain IFCM iteration with V > 1 shells (one thread per voxel,
+// neighbours read straight from global memory), the per-particle reduction
+// that finalises every iteration (Eq 3 centres, Eq 1 objective, stop rule),
+// the run-state initialisation, and the dispatch of the plain iteration (the
+// V = 1 kernel is in plain_kernel.cu).
 #include "ifcm_math.cuh"
 #include "launch.h"
 
@@ -42,13 +43,13 @@ __device__ __noinline__ void shell_mean(const float* __restrict__ u, int X, int 
 // of the cube of Chebyshev radius r), weighted by W_r of Eq 10 and
 // renormalised over the shells that hold an in-volume voxel.
 template <int C>
-__device__ void shell_terms(const PlainArgs& a, const float* __restrict__ u, int X, int Y, int Z,
-                            float xc, float (&H)[C], float (&F)[C]) {
+__device__ void shell_terms(const PlainArgs& a, const ShellArgs& sh, const float* __restrict__ u,
+                            int X, int Y, int Z, float xc, float (&H)[C], float (&F)[C]) {
   const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
   float wsum = 0.0f;
 #pragma unroll
   for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
-  for (int r = 1; r <= a.V; ++r) {
+  for (int r = 1; r <= sh.V; ++r) {
     float hr[C], fr[C], G = 0.0f, Q = 0.0f;
     int n = 0;
 #pragma unroll
@@ -84,7 +85,7 @@ __device__ void shell_terms(const PlainArgs& a, const float* __restrict__ u, int
 #pragma unroll
       for (int j = 0; j < C; ++j) hr[j] = 1.0f / C;
     }
-    const float invQ = __frcp_rn(Q), w = a.W[r - 1];
+    const float invQ = __frcp_rn(Q), w = sh.W[r - 1];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       H[j] = fmaf(w, hr[j], H[j]);
@@ -102,15 +103,20 @@ __device__ void shell_terms(const PlainArgs& a, const float* __restrict__ u, int
   }
 }
 
+// The plain iteration with V > 1 shells (Eq 10, reading R17) for P
+// particles at once (grid y = particle).  The V = 1, one-particle kernel
+// (plain_kernel.cu) is the paper-shaped form and the FCM start; it is
+// compiled apart so that its code stays that of the plain form alone.
 template <int C>
-__global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
+__global__ void __launch_bounds__(PT) plain_shell_kernel(const PlainArgs a, const ShellArgs sh) {
   __shared__ float s_red[PT / 32][2 * C + 2];
   const int pid = blockIdx.y;                  // particle of the launch
   if (!a.active[pid]) return;
   const long long nvox = static_cast<long long>(a.nx) * a.ny * a.nz;
   const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
-  const float* u_src = a.u_src ? a.u_src + pid * a.src_pstride : nullptr;
-  float* u_dst = a.u_dst + pid * a.dst_pstride;
+  // the particle's U^t and U^{t+1}; a.u_src == NULL (u = 1/c) is tested on the
+  // kernel parameter itself so that the test stays uniform and out of the loops
+  const long long soff = pid * sh.src_pstride, doff = pid * sh.dst_pstride;
   MethodConsts k;
   if (a.lam_xi) {
     k.lam = static_cast<float>(a.lam_xi[2 * pid]);
@@ -144,55 +150,18 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     const float xc = a.x[off];
     float uc[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) uc[j] = u_src ? u_src[j * plane + off] : 1.0f / C;
+    for (int j = 0; j < C; ++j) uc[j] = a.u_src ? a.u_src[soff + j * plane + off] : 1.0f / C;
     float H[C], F[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
-    if (stencil && a.V > 1) {
-      shell_terms<C>(a, u_src, X, Y, Z, xc, H, F);
-    } else if (stencil) {
-      float G = 0.0f, Q = 0.0f;
-      int cnt = 0;
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            const int kx = X + dx, ky = Y + dy, kz = Z + dz;
-            if (kx < 0 || kx >= a.nx || ky < 0 || ky >= a.ny || kz < 0 || kz >= a.nz) continue;
-            const size_t ko = (static_cast<size_t>(kz) * a.ny + ky) * a.pitch + kx;
-            const float g = fabsf(xc - a.x[ko]);                       // Eq 6
-            const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);   // Eq 8
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-              const float uk = u_src ? u_src[j * plane + ko] : 1.0f / C;
-              H[j] = fmaf(uk, g, H[j]);
-              F[j] = fmaf(uk * uk, q2, F[j]);
-            }
-            G += g;
-            Q += q2;
-            ++cnt;
-          }
-      if (cnt > 0) {
-        const float invQ = __frcp_rn(Q);
-#pragma unroll
-        for (int j = 0; j < C; ++j) F[j] *= invQ;
-        if (G > 0.0f) {
-          const float invG = __frcp_rn(G);
-#pragma unroll
-          for (int j = 0; j < C; ++j) H[j] *= invG;
-        } else if (u_src) {
-          flat_neighbourhood_mean<C>(u_src, X, Y, Z, a.nx, a.ny, a.nz, a.pitch, H);
-        } else {
-#pragma unroll
-          for (int j = 0; j < C; ++j) H[j] = 1.0f / C;
-        }
-      }
+    if (stencil) {
+      shell_terms<C>(a, sh, a.u_src ? a.u_src + soff : nullptr, X, Y, Z, xc, H, F);
     }
     float u[C], um[C], Jv;
     voxel_update<C>(H, F, xc, cc, k, u, um, Jv);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      u_dst[j * plane + off] = u[j];
+      a.u_dst[doff + j * plane + off] = u[j];
       s0[j] += um[j];
       s1[j] = fmaf(um[j], xc, s1[j]);
       dm = fmaxf(dm, fabsf(u[j] - uc[j]));
@@ -217,7 +186,7 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     s_red[warp][2 * C + 1] = vm;
   }
   __syncthreads();
-  const size_t rec = static_cast<size_t>(pid) * a.n_rec + blockIdx.x;
+  const size_t rec = static_cast<size_t>(pid) * sh.n_rec + blockIdx.x;
   if (threadIdx.x < 2 * C + 1) {
     double sum = 0.0;
 #pragma unroll
@@ -402,15 +371,24 @@ __global__ void run_init_kernel(int P, const double* c0, RunState st, double* J_
 
 }  // namespace
 
+// Defined in plain_kernel.cu.
+cudaError_t launch_plain_v1(int c, const PlainArgs& a, int blocks, cudaStream_t s);
+
 int plain_blocks(long long nvox, int vpt) {
   const long long per = static_cast<long long>(PT) * vpt;
   return static_cast<int>((nvox + per - 1) / per);
 }
 
-cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s) {
-  if (a.P < 1 || a.V < 1 || a.V > kMaxV) return cudaErrorInvalidValue;
-  const dim3 grid(blocks, a.P);
-  PIFCM_DISPATCH_C(c, (plain_kernel<C><<<grid, PT, 0, s>>>(a)); return cudaGetLastError());
+cudaError_t launch_plain(int c, const PlainArgs& a, const ShellArgs& sh, int blocks,
+                         cudaStream_t s) {
+  if (sh.P < 1 || sh.V < 1 || sh.V > kMaxV) return cudaErrorInvalidValue;
+  if (sh.V > 1 && a.stencil) {
+    const dim3 grid(blocks, sh.P);
+    PIFCM_DISPATCH_C(c, (plain_shell_kernel<C><<<grid, PT, 0, s>>>(a, sh));
+                     return cudaGetLastError());
+  }
+  if (sh.P != 1) return cudaErrorInvalidValue;    // V = 1 batches run the stencil kernel
+  return launch_plain_v1(c, a, blocks, s);
 }
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s) {

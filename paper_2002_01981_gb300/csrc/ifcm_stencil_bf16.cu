@@ -7,37 +7,37 @@ namespace pifcm {
 
 size_t smem_bytes_bf16_np1(int c) {
   switch (c) {
-    case 2: return smem_total<2, 1, true>();
-    case 3: return smem_total<3, 1, true>();
-    case 4: return smem_total<4, 1, true>();
-    case 5: return smem_total<5, 1, true>();
-    case 6: return smem_total<6, 1, true>();
-    case 7: return smem_total<7, 1, true>();
-    default: return smem_total<8, 1, true>();
+    case 2: return smem_total<2, 1, UL_BF16>();
+    case 3: return smem_total<3, 1, UL_BF16>();
+    case 4: return smem_total<4, 1, UL_BF16>();
+    case 5: return smem_total<5, 1, UL_BF16>();
+    case 6: return smem_total<6, 1, UL_BF16>();
+    case 7: return smem_total<7, 1, UL_BF16>();
+    default: return smem_total<8, 1, UL_BF16>();
   }
 }
 
 int blocks_per_sm_bf16_np1(int c) {
   switch (c) {
-    case 2: return blocks_per_sm_c<2, 1, true>();
-    case 3: return blocks_per_sm_c<3, 1, true>();
-    case 4: return blocks_per_sm_c<4, 1, true>();
-    case 5: return blocks_per_sm_c<5, 1, true>();
-    case 6: return blocks_per_sm_c<6, 1, true>();
-    case 7: return blocks_per_sm_c<7, 1, true>();
-    default: return blocks_per_sm_c<8, 1, true>();
+    case 2: return blocks_per_sm_c<2, 1, UL_BF16>();
+    case 3: return blocks_per_sm_c<3, 1, UL_BF16>();
+    case 4: return blocks_per_sm_c<4, 1, UL_BF16>();
+    case 5: return blocks_per_sm_c<5, 1, UL_BF16>();
+    case 6: return blocks_per_sm_c<6, 1, UL_BF16>();
+    case 7: return blocks_per_sm_c<7, 1, UL_BF16>();
+    default: return blocks_per_sm_c<8, 1, UL_BF16>();
   }
 }
 
 cudaError_t launch_stencil_bf16_np1(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, 1, true>(a, grid, s);
-    case 3: return launch_c<3, 1, true>(a, grid, s);
-    case 4: return launch_c<4, 1, true>(a, grid, s);
-    case 5: return launch_c<5, 1, true>(a, grid, s);
-    case 6: return launch_c<6, 1, true>(a, grid, s);
-    case 7: return launch_c<7, 1, true>(a, grid, s);
-    case 8: return launch_c<8, 1, true>(a, grid, s);
+    case 2: return launch_c<2, 1, UL_BF16>(a, grid, s);
+    case 3: return launch_c<3, 1, UL_BF16>(a, grid, s);
+    case 4: return launch_c<4, 1, UL_BF16>(a, grid, s);
+    case 5: return launch_c<5, 1, UL_BF16>(a, grid, s);
+    case 6: return launch_c<6, 1, UL_BF16>(a, grid, s);
+    case 7: return launch_c<7, 1, UL_BF16>(a, grid, s);
+    case 8: return launch_c<8, 1, UL_BF16>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

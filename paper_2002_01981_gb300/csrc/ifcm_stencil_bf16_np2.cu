@@ -7,25 +7,25 @@ namespace pifcm {
 
 size_t smem_bytes_bf16_np2(int c) {
   switch (c) {
-    case 2: return smem_total<2, 2, true>();
-    case 3: return smem_total<3, 2, true>();
-    default: return smem_total<4, 2, true>();
+    case 2: return smem_total<2, 2, UL_BF16>();
+    case 3: return smem_total<3, 2, UL_BF16>();
+    default: return smem_total<4, 2, UL_BF16>();
   }
 }
 
 int blocks_per_sm_bf16_np2(int c) {
   switch (c) {
-    case 2: return blocks_per_sm_c<2, 2, true>();
-    case 3: return blocks_per_sm_c<3, 2, true>();
-    default: return blocks_per_sm_c<4, 2, true>();
+    case 2: return blocks_per_sm_c<2, 2, UL_BF16>();
+    case 3: return blocks_per_sm_c<3, 2, UL_BF16>();
+    default: return blocks_per_sm_c<4, 2, UL_BF16>();
   }
 }
 
 cudaError_t launch_stencil_bf16_np2(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, 2, true>(a, grid, s);
-    case 3: return launch_c<3, 2, true>(a, grid, s);
-    case 4: return launch_c<4, 2, true>(a, grid, s);
+    case 2: return launch_c<2, 2, UL_BF16>(a, grid, s);
+    case 3: return launch_c<3, 2, UL_BF16>(a, grid, s);
+    case 4: return launch_c<4, 2, UL_BF16>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

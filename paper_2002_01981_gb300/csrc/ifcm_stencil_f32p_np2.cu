@@ -1,0 +1,33 @@
+// The stencil kernel over float2 pair words with two particles per work item
+// (c <= 4): word (pair k, cluster j) holds cluster j of particles 2k and 2k+1,
+// loaded and stored as one 64-bit access.  The FP32 layout of batched runs.
+#include "stencil_kernel.cuh"
+
+namespace pifcm {
+
+size_t smem_bytes_f32p_np2(int c) {
+  switch (c) {
+    case 2: return smem_total<2, 2, UL_F32P>();
+    case 3: return smem_total<3, 2, UL_F32P>();
+    default: return smem_total<4, 2, UL_F32P>();
+  }
+}
+
+int blocks_per_sm_f32p_np2(int c) {
+  switch (c) {
+    case 2: return blocks_per_sm_c<2, 2, UL_F32P>();
+    case 3: return blocks_per_sm_c<3, 2, UL_F32P>();
+    default: return blocks_per_sm_c<4, 2, UL_F32P>();
+  }
+}
+
+cudaError_t launch_stencil_f32p_np2(int c, const StencilArgs& a, int grid, cudaStream_t s) {
+  switch (c) {
+    case 2: return launch_c<2, 2, UL_F32P>(a, grid, s);
+    case 3: return launch_c<3, 2, UL_F32P>(a, grid, s);
+    case 4: return launch_c<4, 2, UL_F32P>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pifcm

@@ -1,0 +1,45 @@
+// The stencil kernel with FP32 planar memberships and one particle per work
+// item (every c): used by one-particle runs (ifcm_fit, the gradient's forward
+// pass, whose adjoint kernels read planar checkpoints).
+#include "stencil_kernel.cuh"
+
+namespace pifcm {
+
+size_t smem_bytes_planar_np1(int c) {
+  switch (c) {
+    case 2: return smem_total<2, 1, UL_PLANAR>();
+    case 3: return smem_total<3, 1, UL_PLANAR>();
+    case 4: return smem_total<4, 1, UL_PLANAR>();
+    case 5: return smem_total<5, 1, UL_PLANAR>();
+    case 6: return smem_total<6, 1, UL_PLANAR>();
+    case 7: return smem_total<7, 1, UL_PLANAR>();
+    default: return smem_total<8, 1, UL_PLANAR>();
+  }
+}
+
+int blocks_per_sm_planar_np1(int c) {
+  switch (c) {
+    case 2: return blocks_per_sm_c<2, 1, UL_PLANAR>();
+    case 3: return blocks_per_sm_c<3, 1, UL_PLANAR>();
+    case 4: return blocks_per_sm_c<4, 1, UL_PLANAR>();
+    case 5: return blocks_per_sm_c<5, 1, UL_PLANAR>();
+    case 6: return blocks_per_sm_c<6, 1, UL_PLANAR>();
+    case 7: return blocks_per_sm_c<7, 1, UL_PLANAR>();
+    default: return blocks_per_sm_c<8, 1, UL_PLANAR>();
+  }
+}
+
+cudaError_t launch_stencil_planar_np1(int c, const StencilArgs& a, int grid, cudaStream_t s) {
+  switch (c) {
+    case 2: return launch_c<2, 1, UL_PLANAR>(a, grid, s);
+    case 3: return launch_c<3, 1, UL_PLANAR>(a, grid, s);
+    case 4: return launch_c<4, 1, UL_PLANAR>(a, grid, s);
+    case 5: return launch_c<5, 1, UL_PLANAR>(a, grid, s);
+    case 6: return launch_c<6, 1, UL_PLANAR>(a, grid, s);
+    case 7: return launch_c<7, 1, UL_PLANAR>(a, grid, s);
+    case 8: return launch_c<8, 1, UL_PLANAR>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pifcm

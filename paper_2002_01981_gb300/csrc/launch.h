@@ -57,30 +57,30 @@ struct StencilArgs {
 };
 static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
 
+// Layout of the memberships between iterations (see stencil_kernel.cuh):
+// FP32 planes per particle, bf16 pair words, or float2 pair words.
+constexpr int UL_PLANAR = 0, UL_BF16 = 1, UL_F32P = 2;
+
 // np = particles sharing one work item: 1 for every c, 2 for c <= 4.
-// bf16: memberships stored as bf16 pair words (see stencil_kernel.cuh).
 bool stencil_np_supported(int c, int np);
 int stencil_default_np(int c);
-size_t stencil_smem_bytes(int c, int np, bool bf16);
-int stencil_blocks_per_sm(int c, int np, bool bf16);
-cudaError_t launch_stencil(int c, int np, bool bf16, const StencilArgs& a, int grid,
+size_t stencil_smem_bytes(int c, int np, int layout);
+int stencil_blocks_per_sm(int c, int np, int layout);
+cudaError_t launch_stencil(int c, int np, int layout, const StencilArgs& a, int grid,
                            cudaStream_t s);
-// 32-bit words per voxel of one pair-word membership buffer of P particles
+// Pair words per voxel of one pair-word membership buffer of P particles
 // laid out for np: ceil(P/2) * c (np = 2) or P * ceil(c/2) (np = 1).
-long long bf16_unit_words(int c, int np, int P);
+long long pair_unit_words(int c, int np, int P);
 
 // ------------------------------------- plain iteration (one thread per voxel)
-constexpr int kMaxV = 4;            // neighbourhood shells (Eq 10) of the plain kernel
+constexpr int kMaxV = 4;            // neighbourhood shells (Eq 10) of the shell kernel
 
-// Particle p of a launch is blockIdx.y: its U^t at u_src + p * src_pstride,
-// U^{t+1} at u_dst + p * dst_pstride, (lambda, xi) at lam_xi[2p], C^t at
-// centres[p c], records p * n_rec + blockIdx.x.
 struct PlainArgs {
   int nx, ny, nz, pitch;
   const float* x;
   const float* u_src;           // U^t, or NULL for u = 1/c
   float* u_dst;                 // U^{t+1}
-  const double* lam_xi;         // device [P][2], or NULL: use lam / xi below
+  const double* lam_xi;         // device (lambda, xi) [P][2], or NULL: use lam / xi below
   float lam, xi;
   const double* centres;        // [P][c] C^t
   const int32_t* active;        // [P]
@@ -90,17 +90,26 @@ struct PlainArgs {
   int m_is_2;
   int vpt;                      // voxels per thread
   int stencil;                  // 0: lambda = xi = 0, no neighbourhood terms
+  DevStatus* status;
+};
+
+// The V > 1 shell kernel's extra arguments.  Particle p of a launch is
+// blockIdx.y: its U^t at u_src + p * src_pstride, U^{t+1} at u_dst + p *
+// dst_pstride, (lambda, xi) at lam_xi[2p], C^t at centres[p c], records
+// p * n_rec + blockIdx.x.
+struct ShellArgs {
   int P;                        // particles (grid y)
   long long src_pstride;        // elements between particles' U^t (0: one shared U^t)
   long long dst_pstride;        // elements between particles' U^{t+1}
   int n_rec;                    // records per particle (grid x)
   int V;                        // shells, 1..kMaxV
   float W[kMaxV];               // Eq 10 weights W_1..W_V
-  DevStatus* status;
 };
 
 int plain_blocks(long long nvox, int vpt);
-cudaError_t launch_plain(int c, const PlainArgs& a, int blocks, cudaStream_t s);
+// One particle, V = 1 (sh.V == 1, sh.P == 1), or the shell kernel (sh.V > 1).
+cudaError_t launch_plain(int c, const PlainArgs& a, const ShellArgs& sh, int blocks,
+                         cudaStream_t s);
 
 // ---------------------------------------------- per-particle finalisation
 // One volume of a reduce launch (particle p of the volume is state index
@@ -174,13 +183,14 @@ cudaError_t launch_fill(float* dst, float value, long long n, cudaStream_t s);
 cudaError_t launch_select_copy(const float* a, const float* b, const int32_t* iters,
                                float* dst, long long n, cudaStream_t s);
 // Pair words of a shared start: u0 [c][plane] FP32 -> [c][plane] words (u, u)
-// for np = 2, or [ceil(c/2)][plane] words (u_2k, u_2k+1) for np = 1.
-cudaError_t launch_pack_start(const float* u0, uint32_t* out, int c, int np, long long plane,
-                              cudaStream_t s);
+// for np = 2, or [ceil(c/2)][plane] words (u_2k, u_2k+1) for np = 1; bf16x2
+// (layout UL_BF16) or float2 (UL_F32P) words.
+cudaError_t launch_pack_start(const float* u0, void* out, int c, int np, int layout,
+                              long long plane, cudaStream_t s);
 // Particle 0's memberships from the pair-word buffer its last iteration wrote
 // (a after an odd number of iterations, else b) as FP32 [c][plane].
-cudaError_t launch_unpack_select(const uint32_t* a, const uint32_t* b, const int32_t* iters,
-                                 float* dst, int c, int np, long long plane, cudaStream_t s);
+cudaError_t launch_unpack_select(const void* a, const void* b, const int32_t* iters, float* dst,
+                                 int c, int np, int layout, long long plane, cudaStream_t s);
 cudaError_t launch_pso_init(const pso_state& st, cudaStream_t s);
 cudaError_t launch_pso_step(const pso_state& st, const double* fitness, cudaStream_t s);
 cudaError_t launch_pso_best(const double* pbest_x, const double* pbest_f, int P,

@@ -30,7 +30,11 @@
 // within a thread and a warp, FP64 across warps) that the reduce kernel sums
 // per particle in FP64.
 //
-// BF16 memberships (BF = true): U^t and U^{t+1} are stored as bf16 pairs, one
+// Membership layouts (template parameter UL): UL_PLANAR stores each particle's
+// c FP32 planes; the pair-word layouts UL_BF16 and UL_F32P store one word per
+// (voxel, pair) -- bf16x2 (4 bytes) or float2 (8 bytes) -- as described next.
+//
+// BF16 memberships (UL = UL_BF16): U^t and U^{t+1} are stored as bf16 pairs, one
 // 32-bit word per (voxel, pair): the two particles of a fixed pair (2k, 2k+1)
 // for the same cluster when NP = 2, or clusters (2k, 2k+1) of one particle
 // when NP = 1 -- the same pairing as the packed FP32x2 sums, low half first.
@@ -39,7 +43,10 @@
 // one 32-bit store writes one.  All arithmetic stays FP32: a word is unpacked
 // exactly (bf16 -> f32 is a shift) and u' is rounded to nearest even once,
 // when it is stored.  max|du| compares the stored (rounded) values; the sums of
-// Eqs 1 and 3 use the FP32 u' that the rounding was applied to.
+// Eqs 1 and 3 use the FP32 u' that the rounding was applied to.  UL_F32P is
+// the same pairing with float2 words: one 64-bit shared-memory load per pair
+// and no unpacking, one 64-bit store per pair, bit-identical arithmetic to
+// UL_PLANAR.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -87,31 +94,30 @@ template <int C, int NP>
 struct Pairs {
   static constexpr int K = NP == 2 ? C : (C + 1) / 2;
 };
-// 32-bit membership planes of one stage: c per particle in FP32, one per pair
-// in BF16.
-template <int C, int NP, bool BF>
-__host__ __device__ constexpr int uplanes() {
-  return BF ? Pairs<C, NP>::K : NP * C;
-}
-// Bytes of a stage's membership block (every TMA destination 128-B aligned).
-template <int C, int NP, bool BF>
+__host__ __device__ constexpr bool paired(int ul) { return ul != UL_PLANAR; }
+__host__ __device__ constexpr int word_bytes(int ul) { return ul == UL_BF16 ? 4 : 8; }
+// Bytes of a stage's membership block (every TMA destination 128-B aligned):
+// c FP32 planes per particle, or one word plane per pair.
+template <int C, int NP, int UL>
 __host__ __device__ constexpr int ublock_bytes() {
-  return BF ? ((Pairs<C, NP>::K * PLANE * 4 + 127) / 128) * 128 : NP * ubytes<C>();
+  return paired(UL) ? ((Pairs<C, NP>::K * PLANE * word_bytes(UL) + 127) / 128) * 128
+                    : NP * ubytes<C>();
 }
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __host__ __device__ constexpr int stage_bytes() {
-  return XBYTES + ublock_bytes<C, NP, BF>();
+  return XBYTES + ublock_bytes<C, NP, UL>();
 }
 static_assert(XBYTES % 128 == 0 && ubytes<3>() % 128 == 0 && ubytes<5>() % 128 == 0 &&
                   ubytes<7>() % 128 == 0,
               "TMA shared-memory destinations must start on 128-byte boundaries");
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __host__ __device__ constexpr uint32_t stage_tx_bytes() {
-  return static_cast<uint32_t>((1 + uplanes<C, NP, BF>()) * PLANE * 4);
+  return static_cast<uint32_t>(PLANE * 4 + (paired(UL) ? Pairs<C, NP>::K * PLANE * word_bytes(UL)
+                                                        : NP * C * PLANE * 4));
 }
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __host__ __device__ constexpr int smem_total() {
-  return NSTAGE * stage_bytes<C, NP, BF>() + 128;
+  return NSTAGE * stage_bytes<C, NP, UL>() + 128;
 }
 
 __device__ __forceinline__ void consumer_sync() {
@@ -134,7 +140,7 @@ struct Item {
   int p0, p1;          // the volume's particles of the group (p1 = p0 when the group has one)
   bool on0;            // p0 is running (its partial record is written)
   bool two;            // p1 is a distinct, running particle
-  int unit;            // BF16: the pair (NP = 2) or particle (NP = 1) whose words are loaded
+  int unit;            // pair words: the pair (NP = 2) or particle (NP = 1) whose words are loaded
   int tile, x0, y0, z0, z1, pzb, pze;
 };
 
@@ -148,13 +154,13 @@ struct ItemTable {
   int vfirst[kMaxVols], vnact[kMaxVols], vitem[kMaxVols + 1];
 };
 
-// Units of a group: NP particles in FP32, one unit (pair or particle) in BF16.
-template <int NP, bool BF>
+// Units of a group: NP particles (planar), one unit (pair or particle) with pair words.
+template <int NP, int UL>
 __host__ __device__ constexpr int group_units() {
-  return BF ? 1 : NP;
+  return paired(UL) ? 1 : NP;
 }
 
-template <int NP, bool BF>
+template <int NP, int UL>
 __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTable& tab, int w) {
   Item it;
   int v = 0;
@@ -165,7 +171,7 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTabl
   const int g = wl / vd.n_tiles;
   it.tile = wl - g * vd.n_tiles;
   const short* act = tab.act + tab.vfirst[v];
-  if (BF && NP == 2) {
+  if (paired(UL) && NP == 2) {
     const int u = act[g];
     const bool has1 = 2 * u + 1 < vd.P;
     it.unit = u;
@@ -211,9 +217,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float2 v) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __device__ __forceinline__ float2 load_pair(const float* __restrict__ us, int k, int off) {
-  if (BF) return unpack_bf16x2(reinterpret_cast<const uint32_t*>(us)[k * PLANE + off]);
+  if (UL == UL_BF16) return unpack_bf16x2(reinterpret_cast<const uint32_t*>(us)[k * PLANE + off]);
+  if (UL == UL_F32P) return reinterpret_cast<const float2*>(us)[k * PLANE + off];
   if (NP == 2) return make_float2(us[k * PLANE + off], us[ufloats<C>() + k * PLANE + off]);
   const float lo = us[(2 * k) * PLANE + off];
   const float hi = (2 * k + 1 < C) ? us[(2 * k + 1) * PLANE + off] : 0.0f;
@@ -271,7 +278,7 @@ struct ItemConst {
 // the plane's window sums A = sum w and B = sum (dx^2 + dy^2) w (w = u^2): the
 // planes above and below weigh q^2 = 1 + dx^2 + dy^2 (A + B), the same plane
 // dx^2 + dy^2 (B).
-template <int C, int NP, bool BF, bool Z3>
+template <int C, int NP, int UL, bool Z3>
 __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
                                                  const float* __restrict__ us, int cidx,
                                                  float x_lo, float x_mid, float x_hi,
@@ -303,7 +310,7 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
       const float2 gl2 = dup2(gl), gh2 = dup2(gh), gm2 = dup2(gm);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float2 uk = load_pair<C, NP, BF>(us, k, off);
+        const float2 uk = load_pair<C, NP, UL>(us, k, off);
         if (Z3) {
           lo.H[k] = __ffma2_rn(uk, gl2, lo.H[k]);
           hi.H[k] = __ffma2_rn(uk, gh2, hi.H[k]);
@@ -341,7 +348,7 @@ __device__ __forceinline__ float2 max2(float2 v, float lo) {
 // Finalise one centre (its u^t is read from its plane's stage at cus): H and F
 // (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
 // the centre's shares of Eqs 1 and 3, in packed pairs.
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
                                                 int cidx, float xc, int z, bool interior,
                                                 const VolDesc& a, const Item& it,
@@ -378,9 +385,14 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       for (int p = 0; p < NP; ++p) {
         const int pid = p == 0 ? it.p0 : it.p1;
         float Hm[C];
-        if (BF)
+        if (UL == UL_BF16)
           flat_neighbourhood_mean_bf16<C>(
               reinterpret_cast<const uint32_t*>(a.u_src) +
+                  static_cast<long long>(it.unit) * a.src_pstride,
+              NP == 2, p, cx.X, cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
+        else if (UL == UL_F32P)
+          flat_neighbourhood_mean_f32p<C>(
+              reinterpret_cast<const float2*>(a.u_src) +
                   static_cast<long long>(it.unit) * a.src_pstride,
               NP == 2, p, cx.X, cx.Y, z, a.nx, a.ny, a.nz, a.pitch, Hm);
         else
@@ -479,7 +491,27 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
   const int plane = a.nz * a.ny * a.pitch;              // c * plane < 2^31 (host-checked)
   const int voff = z * (a.ny * a.pitch) + cx.col_off;
-  if (BF) {
+  if (UL == UL_F32P) {
+    // one float2 word per pair (padding lane as for bf16 below)
+    float2* dst = reinterpret_cast<float2*>(ic.dst[0]);
+    const float2* cw = reinterpret_cast<const float2*>(cus);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const bool pad_hi = NP == 1 && 2 * q + 1 >= C;
+      const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
+      dst[q * plane + voff] = uq;
+      const float2 old = cw[q * PLANE + cidx];
+      const float e0 = fabsf(uq.x - old.x), e1 = fabsf(uq.y - old.y);
+      if (NP == 2) {
+        acc.dm[0] = fmaxf(acc.dm[0], e0);
+        acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
+      } else {
+        acc.dm[0] = fmaxf(acc.dm[0], pad_hi ? e0 : fmaxf(e0, e1));
+      }
+    }
+    return;
+  }
+  if (UL == UL_BF16) {
     // one rounded pair word per pair; max|du| between stored values
     // (with one particle and an odd c, the high half of the last word is
     // padding: stored as 0 and left out of max|du|)
@@ -514,7 +546,7 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
 }
 
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     stencil_kernel(const __grid_constant__ StencilArgs a) {
   extern __shared__ unsigned char dsmem_raw[];
@@ -531,7 +563,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   const int warp = tid >> 5, lane = tid & 31;
 
   // Active units of every volume, compacted one volume per warp (ballots).
-  constexpr bool kPairUnits = BF && NP == 2;
+  constexpr bool kPairUnits = paired(UL) && NP == 2;
   for (int v = warp; v < a.n_vol; v += NT / 32) {
     const VolDesc& vd = a.vol[v];
     const int units = kPairUnits ? (vd.P + 1) / 2 : vd.P;
@@ -566,7 +598,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     int items = 0;
     for (int v = 0; v < a.n_vol; ++v) {
       tab.vitem[v] = items;
-      constexpr int GU = group_units<NP, BF>();
+      constexpr int GU = group_units<NP, UL>();
       items += ((tab.vnact[v] + GU - 1) / GU) * a.vol[v].n_tiles;
     }
     tab.vitem[a.n_vol] = items;
@@ -576,10 +608,10 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   if (static_cast<int>(blockIdx.x) >= n_items) return;
 
   auto xs_of = [&](int s) {
-    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, BF>());
+    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, UL>());
   };
   auto us_of = [&](int s) {
-    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, BF>() + XBYTES);
+    return reinterpret_cast<float*>(dsmem + s * stage_bytes<C, NP, UL>() + XBYTES);
   };
 
   // ------------------------------------------------------------ producer
@@ -587,7 +619,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     if (lane == 0) {
       int q = 0;
       for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const Item it = decode_item<NP, BF>(a, tab, w);
+        const Item it = decode_item<NP, UL>(a, tab, w);
         const VolDesc& vd = a.vol[it.v];
         const CUtensorMap* mx = &a.tm_x[it.v];
         const CUtensorMap* mu = &a.tm_u[it.v];
@@ -600,11 +632,11 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
             return;
           }
           if (*reinterpret_cast<volatile int*>(&s_abort)) return;
-          mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP, BF>());
+          mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP, UL>());
           tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
           tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                      (BF ? it.unit : it.p0) * vd.src_cstride);
-          if (NP == 2 && !BF)
+                      (paired(UL) ? it.unit : it.p0) * vd.src_cstride);
+          if (NP == 2 && !paired(UL))
             tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
                         it.p1 * vd.src_cstride);
         }
@@ -640,7 +672,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   };
 
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const Item it = decode_item<NP, BF>(a, tab, w);
+    const Item it = decode_item<NP, UL>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
     const bool z3 = vd.nz > 1;
     const int plane = vd.nz * vd.ny * vd.pitch;
@@ -661,8 +693,10 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         for (int j = 0; j < C; ++j)
           cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
         if (p < NP)
-          s_ic.dst[p] = BF ? vd.u_dst + static_cast<size_t>(it.unit) * Pairs<C, NP>::K * plane
-                           : vd.u_dst + static_cast<size_t>(pid) * C * plane;
+          s_ic.dst[p] = paired(UL) ? vd.u_dst + static_cast<size_t>(it.unit) *
+                                                   Pairs<C, NP>::K * plane *
+                                                   (word_bytes(UL) / 4)
+                                   : vd.u_dst + static_cast<size_t>(pid) * C * plane;
       }
       s_ic.nlam = make_float2(-lam[0], -lam[1]);
       s_ic.nxi = make_float2(-xi[0], -xi[1]);
@@ -701,14 +735,14 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         const int zd = pz - 2;
         if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
           const int sdi = (qq + NSTAGE - 2) % NSTAGE;
-          finalize_centre<C, NP, BF>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
+          finalize_centre<C, NP, UL>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
                                  cx.col_interior && zd > 0 && zd < vd.nz - 1, vd, it, s_ic, cx,
                                  k, acc);
         }
         if (z3)
-          accumulate_plane<C, NP, BF, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
         else
-          accumulate_plane<C, NP, BF, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          accumulate_plane<C, NP, UL, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
       }
       if (kk >= 2) release(qq - 2);
       sd = sl;
@@ -723,13 +757,13 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
       if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
         const int sdi = (ql + NSTAGE - 1) % NSTAGE;
-        finalize_centre<C, NP, BF>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
+        finalize_centre<C, NP, UL>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
                                cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
                                it, s_ic, cx, k, acc);
       }
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
         const int sli = ql % NSTAGE;
-        finalize_centre<C, NP, BF>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
+        finalize_centre<C, NP, UL>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
                                cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
       }
       if (np >= 2) release(ql - 1);
@@ -786,23 +820,23 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   }
 }
 // ---------------------------------------------------------------------------
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
-  constexpr int smem = smem_total<C, NP, BF>();
-  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, BF>,
+  constexpr int smem = smem_total<C, NP, UL>();
+  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil_kernel<C, NP, BF><<<grid, NT, smem, s>>>(a);
+  stencil_kernel<C, NP, UL><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int C, int NP, bool BF>
+template <int C, int NP, int UL>
 int blocks_per_sm_c() {
   int n = 0;
-  constexpr int smem = smem_total<C, NP, BF>();
-  cudaFuncSetAttribute(stencil_kernel<C, NP, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int smem = smem_total<C, NP, UL>();
+  cudaFuncSetAttribute(stencil_kernel<C, NP, UL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP, BF>, NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP, UL>, NT, smem) !=
       cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
