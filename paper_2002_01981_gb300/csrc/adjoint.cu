@@ -20,8 +20,11 @@
 //   reduce kernel: the per-block partial sums of lambda_bar, xi_bar and c_bar^t
 //   in FP64 in a fixed order.
 //
-// One thread per voxel, neighbours read from global memory (L1 / L2), FP32
-// arithmetic, per-block partials FP32 within a warp and FP64 across warps.
+// The point kernel marches 32 x 8 column tiles along z with a three-plane
+// shared-memory ring (one-voxel halo, the next plane fetched into registers
+// while the current one is computed); the gather kernel reads global memory.
+// FP32 arithmetic; per-block partials are FP32 within a warp and FP64 across
+// warps.
 #include <math_constants.h>
 
 #include "ifcm_math.cuh"
@@ -31,62 +34,94 @@ namespace pifcm {
 
 namespace {
 
-constexpr int AT = 256;   // threads per block
+// Tiles: 32 x 8 columns per block (one thread per column), marched along z
+// over chunks of AZ planes.  Each step keeps three planes (z - 1, z, z + 1) of
+// the needed channels with a one-voxel halo in a shared-memory ring; a plane
+// is loaded cooperatively with coalesced row reads.  Positions outside the
+// volume are filled so that they contribute nothing without masks: the
+// volume x with NaN (g = max(|x_i - x_k|, 0) turns it into 0), every other
+// channel with 0.
+constexpr int ATX = 32, ATY = 8, AT = ATX * ATY;
+constexpr int AZ = 8;
+constexpr int HX = ATX + 2, HY = ATY + 2, HP = HX * HY;   // halo plane cells
 
-// H, F of Eqs 5 and 7 from U^t at voxel (X, Y, Z), with G = sum g, Q = sum q^2
-// and the in-volume neighbour count n.
-template <int C>
-__device__ __forceinline__ void neighbour_terms(const AdjointArgs& a, int X, int Y, int Z,
-                                                float xc, size_t plane, float (&H)[C],
-                                                float (&F)[C], float& G, float& Q, int& n) {
+__device__ __forceinline__ float gdist_nan0(float a, float b) {
+  float r;
+  asm("max.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(fabsf(a - b)));
+  return r;
+}
+
+struct TileGeo {
+  int x0, y0, z0, z1;
+};
+
+__device__ __forceinline__ TileGeo tile_of(const AdjointArgs& a) {
+  const int tx = (a.nx + ATX - 1) / ATX, ty = (a.ny + ATY - 1) / ATY;
+  int b = blockIdx.x;
+  const int bx = b % tx;
+  b /= tx;
+  const int by = b % ty;
+  const int bz = b / ty;
+  TileGeo t;
+  t.x0 = bx * ATX;
+  t.y0 = by * ATY;
+  t.z0 = bz * AZ;
+  t.z1 = min(t.z0 + AZ, a.nz);
+  return t;
+}
+
+// Plane z of NCH channels, gathered into registers: element i = threadIdx.x +
+// k AT of the [NCH][HP] plane.  Channel 0 is the volume x (NaN outside),
+// channels 1.. come from src[ch - 1] (0 outside).  The loads are issued here
+// and consumed later (store_plane), so their latency overlaps the stencil.
+template <int NCH>
+struct PlaneRegs {
+  static constexpr int K = (NCH * HP + AT - 1) / AT;
+  float v[K];
+};
+
+template <int NCH>
+__device__ __forceinline__ void fetch_plane(const AdjointArgs& a, const TileGeo& t, int z,
+                                            const float* const (&src)[NCH - 1],
+                                            PlaneRegs<NCH>& r) {
+  const bool zin = z >= 0 && z < a.nz;
 #pragma unroll
-  for (int j = 0; j < C; ++j) H[j] = F[j] = 0.0f;
-  G = 0.0f;
-  Q = 0.0f;
-  n = 0;
-  float S[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) S[j] = 0.0f;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        const int kx = X + dx, ky = Y + dy, kz = Z + dz;
-        if (kx < 0 || kx >= a.nx || ky < 0 || ky >= a.ny || kz < 0 || kz >= a.nz) continue;
-        const size_t ko = (static_cast<size_t>(kz) * a.ny + ky) * a.pitch + kx;
-        const float g = fabsf(xc - a.x[ko]);
-        const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const float uk = a.u[j * plane + ko];
-          H[j] = fmaf(uk, g, H[j]);
-          F[j] = fmaf(uk * uk, q2, F[j]);
-          S[j] += uk;
-        }
-        G += g;
-        Q += q2;
-        ++n;
+  for (int k = 0; k < PlaneRegs<NCH>::K; ++k) {
+    const int i = threadIdx.x + k * AT;
+    float v = 0.0f;
+    if (i < NCH * HP) {
+      const int ch = i / HP, cell = i - ch * HP;
+      const int cy = cell / HX, cx = cell - cy * HX;
+      const int X = t.x0 - 1 + cx, Y = t.y0 - 1 + cy;
+      v = ch == 0 ? __int_as_float(0x7fc00000) : 0.0f;
+      if (zin && X >= 0 && X < a.nx && Y >= 0 && Y < a.ny) {
+        const size_t off = (static_cast<size_t>(z) * a.ny + Y) * a.pitch + X;
+        v = ch == 0 ? a.x[off] : src[ch - 1][off];
       }
-  if (n == 0) return;                          // no neighbours: H = F = 0
-  const float invQ = __frcp_rn(Q);
+    }
+    r.v[k] = v;
+  }
+}
+
+template <int NCH>
+__device__ __forceinline__ void store_plane(const PlaneRegs<NCH>& r, float* dst) {
 #pragma unroll
-  for (int j = 0; j < C; ++j) F[j] *= invQ;
-  if (G > 0.0f) {
-    const float invG = __frcp_rn(G);
-#pragma unroll
-    for (int j = 0; j < C; ++j) H[j] *= invG;
-  } else {                                     // reading R3: plain mean
-    const float inv = __frcp_rn(static_cast<float>(n));
-#pragma unroll
-    for (int j = 0; j < C; ++j) H[j] = S[j] * inv;
+  for (int k = 0; k < PlaneRegs<NCH>::K; ++k) {
+    const int i = threadIdx.x + k * AT;
+    if (i < NCH * HP) dst[i] = r.v[k];
   }
 }
 
 template <int C>
 __global__ void __launch_bounds__(AT) adjoint_point_kernel(const AdjointArgs a) {
+  extern __shared__ float ring[];                   // [3][1 + C][HP]
   __shared__ float s_red[AT / 32][2 + C];
-  const long long nvox = static_cast<long long>(a.nx) * a.ny * a.nz;
+  constexpr int NCH = 1 + C;
+  const TileGeo t = tile_of(a);
   const size_t plane = static_cast<size_t>(a.nz) * a.ny * a.pitch;
+  const float* srcs[NCH - 1];
+#pragma unroll
+  for (int j = 0; j < C; ++j) srcs[j] = a.u + j * plane;
   const float lam = static_cast<float>(a.lam_xi[0]), xi = static_cast<float>(a.lam_xi[1]);
   float ct[C], cn[C], cb[C];
 #pragma unroll
@@ -102,60 +137,117 @@ __global__ void __launch_bounds__(AT) adjoint_point_kernel(const AdjointArgs a) 
 #pragma unroll
   for (int j = 0; j < C; ++j) cbt[j] = 0.0f;
 
-  for (long long i = blockIdx.x * static_cast<long long>(AT) + threadIdx.x; i < nvox;
-       i += static_cast<long long>(gridDim.x) * AT) {
-    const int X = static_cast<int>(i % a.nx);
-    const long long yz = i / a.nx;
-    const int Y = static_cast<int>(yz % a.ny);
-    const int Z = static_cast<int>(yz / a.ny);
-    const size_t off = (static_cast<size_t>(Z) * a.ny + Y) * a.pitch + X;
-    const float xc = a.x[off];
-    float H[C], F[C], G, Q;
-    int n;
-    neighbour_terms<C>(a, X, Y, Z, xc, plane, H, F, G, Q, n);
-    // Eq 4 (reading R2) and Eq 2
-    float D[C], f[C], fac[C], P[C], d2[C], u[C];
-    float S = 0.0f;
+  const int tx = threadIdx.x % ATX, ty = threadIdx.x / ATX;
+  const int X = t.x0 + tx, Y = t.y0 + ty;
+  const bool col_ok = X < a.nx && Y < a.ny;
+  // ring slot of plane z: z mod 3; planes z0 - 1 and z0 first, then plane
+  // Z + 1 is fetched before plane Z is computed and stored after it
+  PlaneRegs<NCH> pr;
+  fetch_plane<NCH>(a, t, t.z0 - 1, srcs, pr);
+  store_plane<NCH>(pr, ring + ((t.z0 + 2) % 3) * NCH * HP);
+  fetch_plane<NCH>(a, t, t.z0, srcs, pr);
+  store_plane<NCH>(pr, ring + (t.z0 % 3) * NCH * HP);
+  fetch_plane<NCH>(a, t, t.z0 + 1, srcs, pr);
+  store_plane<NCH>(pr, ring + ((t.z0 + 1) % 3) * NCH * HP);
+  __syncthreads();
+  for (int Z = t.z0; Z < t.z1; ++Z) {
+    if (Z + 1 < t.z1) fetch_plane<NCH>(a, t, Z + 2, srcs, pr);
+    if (col_ok) {
+      const float* pm = ring + (Z % 3) * NCH * HP;
+      const int cc = (ty + 1) * HX + tx + 1;
+      const float xc = pm[cc];
+      float H[C], F[C], S[C], G = 0.0f;
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const float dd = xc - ct[j];
-      D[j] = dd * dd;
-      f[j] = 1.0f - lam * H[j] - xi * F[j];
-      fac[j] = fmaxf(f[j], 0.0f);
-      P[j] = D[j] * fac[j];
-      d2[j] = fmaxf(P[j], a.dist_floor);
-      u[j] = a.m_is_2 ? __frcp_rn(d2[j]) : exp2f(-a.inv_m1 * log2f(d2[j]));
-      S += u[j];
+      for (int j = 0; j < C; ++j) H[j] = F[j] = S[j] = 0.0f;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        const float* pl = ring + ((Z + dz + 3) % 3) * NCH * HP;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const int o = cc + dy * HX + dx;
+            const float g = gdist_nan0(xc, pl[o]);
+            const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+              const float uk = pl[(1 + j) * HP + o];
+              H[j] = fmaf(uk, g, H[j]);
+              F[j] = fmaf(uk * uk, q2, F[j]);
+              S[j] += uk;
+            }
+            G += g;
+          }
+      }
+      int n;
+      float Q;
+      box_counts(X, Y, Z, a.nx, a.ny, a.nz, n, Q);
+      if (n > 0) {
+        const float invQ = __frcp_rn(Q);
+#pragma unroll
+        for (int j = 0; j < C; ++j) F[j] *= invQ;
+        if (G > 0.0f) {
+          const float invG = __frcp_rn(G);
+#pragma unroll
+          for (int j = 0; j < C; ++j) H[j] *= invG;
+        } else {                                 // reading R3: plain mean
+          const float inv = __frcp_rn(static_cast<float>(n));
+#pragma unroll
+          for (int j = 0; j < C; ++j) H[j] = S[j] * inv;
+        }
+      }
+      const size_t off = (static_cast<size_t>(Z) * a.ny + Y) * a.pitch + X;
+      // Eq 4 (reading R2) and Eq 2
+      float D[C], f[C], fac[C], P[C], d2[C], u[C];
+      float Ssum = 0.0f;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float dd = xc - ct[j];
+        D[j] = dd * dd;
+        f[j] = 1.0f - lam * H[j] - xi * F[j];
+        fac[j] = fmaxf(f[j], 0.0f);
+        P[j] = D[j] * fac[j];
+        d2[j] = fmaxf(P[j], a.dist_floor);
+        u[j] = a.m_is_2 ? __frcp_rn(d2[j]) : exp2f(-a.inv_m1 * log2f(d2[j]));
+        Ssum += u[j];
+      }
+      const float invS = __frcp_rn(Ssum);
+#pragma unroll
+      for (int j = 0; j < C; ++j) u[j] *= invS;
+      // adjoints
+      float ut[C], um[C];
+      float dot = 0.0f;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float um1 = a.m_is_2 ? u[j] : exp2f((a.m - 1.0f) * log2f(u[j]));   // u^(m-1)
+        um[j] = um1 * u[j];                                                      // u^m
+        const float wb = Jb * d2[j] + cb[j] * (xc - cn[j]);
+        const float ub = a.ubar_next ? a.ubar_next[j * plane + off] : 0.0f;
+        ut[j] = ub + a.m * um1 * wb;
+        dot = fmaf(ut[j], u[j], dot);
+      }
+      const float invG = G > 0.0f ? __frcp_rn(G)
+                                  : (n > 0 ? __frcp_rn(static_cast<float>(n)) : 0.0f);
+      const float invQ = n > 0 ? __frcp_rn(Q) : 0.0f;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float d2b = Jb * um[j] - p * (ut[j] - dot) * u[j] / d2[j];
+        const float Pb = P[j] > a.dist_floor ? d2b : 0.0f;
+        const float fb = f[j] > 0.0f ? Pb * D[j] : 0.0f;
+        lb = fmaf(-fb, H[j], lb);
+        xb = fmaf(-fb, F[j], xb);
+        cbt[j] = fmaf(-2.0f * Pb * fac[j], xc - ct[j], cbt[j]);
+        a.A[j * plane + off] = -lam * fb * invG;
+        a.B[j * plane + off] = -xi * fb * invQ;
+      }
+      a.e[off] = (n > 0 && G == 0.0f) ? 1.0f : 0.0f;
     }
-    const float invS = __frcp_rn(S);
-#pragma unroll
-    for (int j = 0; j < C; ++j) u[j] *= invS;
-    // adjoints
-    float ut[C], um[C];
-    float dot = 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const float um1 = a.m_is_2 ? u[j] : exp2f((a.m - 1.0f) * log2f(u[j]));   // u^(m-1)
-      um[j] = um1 * u[j];                                                      // u^m
-      const float wb = Jb * d2[j] + cb[j] * (xc - cn[j]);
-      const float ub = a.ubar_next ? a.ubar_next[j * plane + off] : 0.0f;
-      ut[j] = ub + a.m * um1 * wb;
-      dot = fmaf(ut[j], u[j], dot);
+    __syncthreads();                     // slot (Z - 1) mod 3 is free
+    if (Z + 1 < t.z1) {
+      store_plane<NCH>(pr, ring + ((Z + 2) % 3) * NCH * HP);
+      __syncthreads();
     }
-    const float invG = G > 0.0f ? __frcp_rn(G) : (n > 0 ? __frcp_rn(static_cast<float>(n)) : 0.0f);
-    const float invQ = n > 0 ? __frcp_rn(Q) : 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const float d2b = Jb * um[j] - p * (ut[j] - dot) * u[j] / d2[j];
-      const float Pb = P[j] > a.dist_floor ? d2b : 0.0f;
-      const float fb = f[j] > 0.0f ? Pb * D[j] : 0.0f;
-      lb = fmaf(-fb, H[j], lb);
-      xb = fmaf(-fb, F[j], xb);
-      cbt[j] = fmaf(-2.0f * Pb * fac[j], xc - ct[j], cbt[j]);
-      a.A[j * plane + off] = -lam * fb * invG;
-      a.B[j * plane + off] = -xi * fb * invQ;
-    }
-    a.e[off] = (n > 0 && G == 0.0f) ? 1.0f : 0.0f;
   }
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,6 +270,9 @@ __global__ void __launch_bounds__(AT) adjoint_point_kernel(const AdjointArgs a) 
   }
 }
 
+// The transposed stencil reads its 26 neighbours' coefficients straight from
+// global memory (L1 / L2), one thread per voxel: with little arithmetic per
+// voxel and 2c + 2 channels, staging planes in shared memory measured slower.
 template <int C>
 __global__ void __launch_bounds__(AT) adjoint_gather_kernel(const AdjointArgs a) {
   const long long nvox = static_cast<long long>(a.nx) * a.ny * a.nz;
@@ -274,19 +369,28 @@ __global__ void polish_step_kernel(double* lam_xi, const double* grad, const dou
 
 }  // namespace
 
-int adjoint_blocks(long long nvox) {
-  long long b = (nvox + AT - 1) / AT;
-  const long long cap = 152LL * 8;
-  if (b > cap) b = cap;
-  return b < 1 ? 1 : static_cast<int>(b);
+int adjoint_blocks(int nx, int ny, int nz) {
+  return ((nx + ATX - 1) / ATX) * ((ny + ATY - 1) / ATY) * ((nz + AZ - 1) / AZ);
+}
+
+template <int C>
+cudaError_t launch_point_c(const AdjointArgs& a, int blocks, cudaStream_t s) {
+  const int smem = 3 * (1 + C) * HP * static_cast<int>(sizeof(float));
+  cudaError_t e = cudaFuncSetAttribute(adjoint_point_kernel<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  adjoint_point_kernel<C><<<blocks, AT, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_point(int c, const AdjointArgs& a, int blocks, cudaStream_t s) {
-  PIFCM_ADJ_DISPATCH(c, (adjoint_point_kernel<C><<<blocks, AT, 0, s>>>(a));
-                     return cudaGetLastError());
+  PIFCM_ADJ_DISPATCH(c, return launch_point_c<C>(a, blocks, s));
 }
 
-cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, int blocks, cudaStream_t s) {
+cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, cudaStream_t s) {
+  long long b = (static_cast<long long>(a.nx) * a.ny * a.nz + AT - 1) / AT;
+  if (b > 152LL * 8) b = 152LL * 8;                 // grid-stride beyond 8 blocks per SM
+  const int blocks = b < 1 ? 1 : static_cast<int>(b);
   PIFCM_ADJ_DISPATCH(c, (adjoint_gather_kernel<C><<<blocks, AT, 0, s>>>(a));
                      return cudaGetLastError());
 }

@@ -1522,7 +1522,7 @@ GradBufs carve_grad(Carver& cv, const ifcm_shape& s, int c, int K) {
   g.e = cv.take<float>(pl);
   g.ubar[0] = cv.take<float>(static_cast<size_t>(c) * pl);
   g.ubar[1] = cv.take<float>(static_cast<size_t>(c) * pl);
-  g.partials = cv.take<double>(static_cast<size_t>(adjoint_blocks(nvox)) * (2 + c));
+  g.partials = cv.take<double>(static_cast<size_t>(adjoint_blocks(s.nx, s.ny, s.nz)) * (2 + c));
   g.cbar = cv.take<double>(c);
   g.best = cv.take<double>(3);
   g.grad = cv.take<double>(2);
@@ -1584,7 +1584,7 @@ ifcm_status grad_reverse(const float* x, const ifcm_shape& s, const ifcm_params*
   const int c = p->c;
   const size_t pl = plane_elems(s);
   const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
-  const int blocks = adjoint_blocks(nvox);
+  const int blocks = adjoint_blocks(s.nx, s.ny, s.nz);
   const size_t tw = 2 * c + 1;
   CU_TRY(cudaMemsetAsync(grad, 0, 2 * sizeof(double), st));
   AdjointArgs a{};
@@ -1618,7 +1618,7 @@ ifcm_status grad_reverse(const float* x, const ifcm_shape& s, const ifcm_params*
     CU_TRY(launch_adjoint_reduce(c, g.partials, blocks, grad, g.cbar, st));
     if (t > 0) {
       ev_beg = prof_begin(st, &ev_end, IFCM_PROF_ADJOINT_GATHER);
-      CU_TRY(launch_adjoint_gather(c, a, blocks, st));
+      CU_TRY(launch_adjoint_gather(c, a, st));
       if (ev_beg) cudaEventRecord(ev_end, st);
     }
   }

@@ -161,9 +161,11 @@ struct AdjointArgs {
   int m_is_2;
 };
 
-int adjoint_blocks(long long nvox);
+// Blocks (and partial records) of the reverse pass's point kernel: 32 x 8
+// column tiles times z-chunks of 8 planes.
+int adjoint_blocks(int nx, int ny, int nz);
 cudaError_t launch_adjoint_point(int c, const AdjointArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_reduce(int c, const double* partials, int blocks, double* grad,
                                   double* cbar_out, cudaStream_t s);
 // mode 0: start (best = current, +inf); 1: keep the best, take a step; 2: keep
