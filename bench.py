@@ -135,8 +135,8 @@ def rank_seed(rank):
 
 def stencil_source_sha():
     h = hashlib.sha256()
-    for name in ("stencil_kernel.cuh", "ifcm_stencil.cu", "ifcm_stencil_np2.cu", "ifcm_math.cuh",
-                 "common.cuh", "launch.h", "api.cu"):
+    for name in ("stencil_kernel.cuh", "ifcm_stencil.cu", "ifcm_stencil_f32p_np2.cu",
+                 "ifcm_math.cuh", "common.cuh", "launch.h", "api.cu"):
         with open(os.path.join(ROOT, "paper_2002_01981_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -653,9 +653,9 @@ def run_ours(args):
                 "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic_pu * per_launch_updates if traffic_pu else None,
                 "algorithmic_bytes_per_launch": per_launch_updates * bytes_per_update,
-                "kernel": f"stencil_kernel<4,{plan_np}>",
+                "kernel": f"stencil_kernel<4,{plan_np},UL_F32P>",
                 "plan": {"particles_per_item": plan_np, "tz": plan_tz,
-                         "tile": "32x11 columns"},
+                         "tile": "32x11 columns", "memberships": "float2 pair words"},
                 "kernel_ms_total": kernel_ms,
                 "kernel_launches": kernel_launches,
                 "kernel_share_of_step": kernel_ms / ms}
