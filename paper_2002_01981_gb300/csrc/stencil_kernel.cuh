@@ -275,9 +275,11 @@ struct ItemConst {
 
 // Contributions of one plane (x in xs, memberships of particle p at us + p *
 // ufloats<C>()) to the centres below (lo), in (mid) and above (hi) it.  F uses
-// the plane's window sums A = sum w and B = sum (dx^2 + dy^2) w (w = u^2): the
-// planes above and below weigh q^2 = 1 + dx^2 + dy^2 (A + B), the same plane
-// dx^2 + dy^2 (B).
+// the plane's window sums of w = u^2 over the centre (W0), the four face
+// neighbours (S1, dx^2 + dy^2 = 1) and the four corners (S2, = 2), each
+// square fused into its sum: the planes above and below weigh q^2 =
+// 1 + dx^2 + dy^2, i.e. W0 + 2 S1 + 3 S2; the same plane dx^2 + dy^2, i.e.
+// S1 + 2 S2.
 template <int C, int NP, int UL, bool Z3>
 __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
                                                  const float* __restrict__ us, int cidx,
@@ -285,9 +287,7 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
                                                  Slot<C, NP>& lo, Slot<C, NP>& mid,
                                                  Slot<C, NP>& hi) {
   constexpr int K = Pairs<C, NP>::K;
-  float2 A[K], B[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) A[k] = B[k] = make_float2(0.0f, 0.0f);
+  float2 W0[K], S1[K], S2[K];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
@@ -296,6 +296,7 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
       const float xk = xs[off];
       const bool self = (dx == 0 && dy == 0);
       const int q2 = dx * dx + dy * dy;          // folded after unrolling
+      const bool first_face = (dy == -1 && dx == 0), first_corner = (dy == -1 && dx == -1);
       float gl = 0.0f, gh = 0.0f, gm = 0.0f;
       if (Z3) {
         gl = gdist(x_lo, xk);
@@ -316,21 +317,21 @@ __device__ __forceinline__ void accumulate_plane(const float* __restrict__ xs,
           hi.H[k] = __ffma2_rn(uk, gh2, hi.H[k]);
         }
         if (!self) mid.H[k] = __ffma2_rn(uk, gm2, mid.H[k]);
-        const float2 wk = __fmul2_rn(uk, uk);
-        A[k] = __fadd2_rn(A[k], wk);
-        if (q2 == 1) B[k] = __fadd2_rn(B[k], wk);
-        if (q2 == 2) B[k] = __ffma2_rn(dup2(2.0f), wk, B[k]);
+        if (self) W0[k] = __fmul2_rn(uk, uk);
+        else if (q2 == 1) S1[k] = first_face ? __fmul2_rn(uk, uk) : __ffma2_rn(uk, uk, S1[k]);
+        else S2[k] = first_corner ? __fmul2_rn(uk, uk) : __ffma2_rn(uk, uk, S2[k]);
       }
     }
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
+    const float2 B = __ffma2_rn(dup2(2.0f), S2[k], S1[k]);           // S1 + 2 S2
     if (Z3) {
-      const float2 ab = __fadd2_rn(A[k], B[k]);
+      const float2 ab = __fadd2_rn(__fadd2_rn(W0[k], S1[k]), __fadd2_rn(S2[k], B));
       lo.F[k] = __fadd2_rn(lo.F[k], ab);
       hi.F[k] = __fadd2_rn(hi.F[k], ab);
     }
-    mid.F[k] = __fadd2_rn(mid.F[k], B[k]);
+    mid.F[k] = __fadd2_rn(mid.F[k], B);
   }
 }
 

@@ -128,15 +128,18 @@ def test_pifcm3d_with_shells(G):
     assert abs(res["J"] - ref["J"]) <= 1e-4 * abs(ref["J"])
 
 
-def j_tol(ref):
-    """J tolerance at the swarm's best personal best: 1e-5, except where that
-    point lies in the clamp regime (lambda + xi > 1, reading R2).  There d^2
-    sits at its floor at many voxels, J shrinks by orders of magnitude, and
-    FP32 rounding of the few unclamped terms dominates it.  The test then
-    allows 1e-3."""
+def j_bound(ref, nvox, dist_floor=1e-12):
+    """|J_gpu - J_oracle| allowed at the swarm's best personal best: 1e-5
+    relative, plus, where that point lies in the clamp regime (lambda + xi >
+    1, reading R2), nvox * dist_floor.  There the factor 1 - lambda H - xi F
+    is exactly 0 at many voxels with crisp memberships (e.g. H + F = 1 at a
+    boundary between two classes), FP32 and FP64 rounding put such a voxel on
+    different sides of the clamp, and each such decision moves J by at most
+    about one floored d^2 (J itself is then a sum of floor-sized terms)."""
     b = int(np.argmin(ref["pbest_f"]))
     lam, xi = ref["swarm"].pbest_x[b]
-    return J_RTOL if lam + xi <= 1.0 else 1e-3
+    J = ref["pbest_f"].min()
+    return J_RTOL * J + (nvox * dist_floor if lam + xi > 1.0 else 0.0)
 
 
 def test_pifcm3d_onestep_fitness(G):
@@ -148,7 +151,7 @@ def test_pifcm3d_onestep_fitness(G):
                      init_max_iter=40, fitness="onestep")
     assert res["status"] == 0
     assert res["lambda"] == ref["lambda"] and res["xi"] == ref["xi"]
-    assert abs(res["best_fitness"] - ref["pbest_f"].min()) <= j_tol(ref) * ref["pbest_f"].min()
+    assert abs(res["best_fitness"] - ref["pbest_f"].min()) <= j_bound(ref, raw.size)
     x = O.normalize(raw)
     U0, C0, _, _ = O.fcm_init(x, 4, 2.0, 40, 0.0)
     bound = u_bound(x, U0, C0, ref["lambda"], ref["xi"], 8)
@@ -167,4 +170,4 @@ def test_onestep_swarm_matches_oracle_each_generation(G):
         ref = OP.pifcm3d(raw, c=3, P=4, generations=gens, seed=3, max_iter=5, eps=0.0,
                          init_max_iter=25, fitness="onestep")
         assert res["lambda"] == ref["lambda"] and res["xi"] == ref["xi"]
-        assert abs(res["best_fitness"] - ref["pbest_f"].min()) <= j_tol(ref) * ref["pbest_f"].min()
+        assert abs(res["best_fitness"] - ref["pbest_f"].min()) <= j_bound(ref, raw.size)
