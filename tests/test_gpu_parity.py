@@ -316,6 +316,23 @@ def test_pifcm3d_host_equals_device(G):
     assert torch.equal(Ud.cpu()[..., :14], uh[..., :14])
 
 
+@pytest.mark.parametrize("slice_z", [-1, 2])
+def test_split_swarm_on_one_rank_equals_pifcm3d(G, slice_z):
+    # the split driver (fitness slices + allgather + identical swarm steps)
+    # with a single rank runs exactly pifcm3d's launches
+    from paper_2002_01981_gb300 import distributed as D
+    raw = phantoms.brain_phantom((6, 20, 22), seed=12, sigma=0.05)
+    prm = G.Params(c=3, max_iter=6, eps_u=1e-5)
+    opts = G.Options(P=5, generations=3, seed=4, init_max_iter=40, slice_z=slice_z)
+    Ua, ra = G.pifcm3d(dev_vol(raw), prm, opts, nx=22)
+    Ub, rb = D.pifcm3d_split(dev_vol(raw), prm, opts, nx=22)
+    assert (rb["lambda"], rb["xi"]) == (ra["lambda"], ra["xi"])
+    assert rb["J"] == ra["J"] and rb["best_fitness"] == ra["best_fitness"]
+    assert rb["iters_final"] == ra["iters_final"] and rb["iters_init"] == ra["iters_init"]
+    assert np.array_equal(rb["centres"], np.asarray(ra["centres"]))
+    assert torch.equal(Ua[..., :22], Ub[..., :22])
+
+
 def test_pifcm3d_slice_mode(G):
     raw = phantoms.brain_phantom((6, 20, 22), seed=8)
     prm = G.Params(c=3, max_iter=5, eps_u=0.0)
