@@ -414,15 +414,15 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       }
     }
   }
-  // Eq 4 with reading R2
+  // Eq 4 with reading R2: d2 = max(D max(f, 0), floor) = max(D f, floor) for
+  // D >= 0 and floor > 0, so the factor needs no clamp of its own
   const float2 one2 = dup2(1.0f), xc2 = dup2(xc);
   float2 d2[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    const float2 fac =
-        max2(__ffma2_rn(ic.nxi, F[q], __ffma2_rn(ic.nlam, H[q], one2)), 0.0f);
+    const float2 f = __ffma2_rn(ic.nxi, F[q], __ffma2_rn(ic.nlam, H[q], one2));
     const float2 dd = __fadd2_rn(xc2, ic.ncc[q]);
-    d2[q] = max2(__fmul2_rn(__fmul2_rn(dd, dd), fac), k.dist_floor);
+    d2[q] = max2(__fmul2_rn(__fmul2_rn(dd, dd), f), k.dist_floor);
   }
   // Eq 2
   float2 u[K], um[K];
@@ -501,8 +501,8 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       const bool pad_hi = NP == 1 && 2 * q + 1 >= C;
       const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
       dst[q * plane + voff] = uq;
-      const float2 old = cw[q * PLANE + cidx];
-      const float e0 = fabsf(uq.x - old.x), e1 = fabsf(uq.y - old.y);
+      const float2 e = __ffma2_rn(cw[q * PLANE + cidx], dup2(-1.0f), uq);   // u' - u
+      const float e0 = fabsf(e.x), e1 = fabsf(e.y);
       if (NP == 2) {
         acc.dm[0] = fmaxf(acc.dm[0], e0);
         acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
@@ -524,8 +524,9 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
       const uint32_t w = pack_bf16x2(uq);
       dst[q * plane + voff] = w;
-      const float2 nr = unpack_bf16x2(w), old = unpack_bf16x2(cw[q * PLANE + cidx]);
-      const float e0 = fabsf(nr.x - old.x), e1 = fabsf(nr.y - old.y);
+      const float2 e = __ffma2_rn(unpack_bf16x2(cw[q * PLANE + cidx]), dup2(-1.0f),
+                                  unpack_bf16x2(w));                       // u' - u
+      const float e0 = fabsf(e.x), e1 = fabsf(e.y);
       if (NP == 2) {
         acc.dm[0] = fmaxf(acc.dm[0], e0);
         acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
