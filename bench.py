@@ -157,11 +157,13 @@ def stencil_traffic_per_update():
 
 
 def launches_per_run(init_iters_launched, generations, max_iter):
-    # normalise (2) + FCM start (2 per iteration + copy) + swarm init
-    # + per generation (state init + 2 per iteration + swarm step)
-    # + best + final run (state init + 2 per iteration + copy) + result
-    return (2 + 2 * init_iters_launched + 1 + 1 + generations * (1 + 2 * max_iter + 1) + 1 +
-            (1 + 2 * max_iter + 1) + 1)
+    # normalise (2) + FCM start (state init + 2 per iteration + copy) + swarm
+    # init + per generation (state init + start packing into pair words + 2 per
+    # iteration + swarm step) + best + final run (state init + start packing +
+    # 2 per iteration + copy) + result.  Checked against the ncu launch list of
+    # one run (3800 launches at 300 / 30 / 50).
+    return (2 + 1 + 2 * init_iters_launched + 1 + 1 +
+            generations * (1 + 1 + 2 * max_iter + 1) + 1 + (1 + 1 + 2 * max_iter + 1) + 1)
 
 
 def plain_form_rate(G, vol, nx, prm, opts, stream, particles=2):
