@@ -475,6 +475,61 @@ def differentiation_leg(G, phantoms, dev):
     return out
 
 
+# ---------------------------------------------------- 2D size sweep (Table 7)
+SWEEP_WORKLOAD = ("n x n slices of the brain stand-in (Rician sigma 0.07), n = 32, 55, 95, 165, "
+                  "285, 493, 854 (the sizes of the paper's Table 7); one whole Algorithm 1 run "
+                  "each: c=4, m=2, 8-neighbourhood, 20 particles x 30 generations, <= 50 "
+                  "iterations per fitness, stop max|du|<1e-5, FCM start <= 300 iterations")
+
+
+def sweep_leg(G, phantoms, dev, runs=2):
+    """Whole Algorithm 1 runs on the 2D sweep: seconds per run (mean of
+    `runs` after one warm run, CUDA events) and updates/s.  Small slices are
+    bound by launch latency (~3800 launches per run), large ones by the
+    stencil."""
+    import torch
+    out = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for n in phantoms.SWEEP_SIZES:
+        raw = phantoms.brain_slice(n, seed=2, sigma=0.07)
+        vol = torch.from_numpy(phantoms.pad_pitch(raw)).to(dev)
+        prm = G.Params(c=C, m=M, max_iter=MAX_ITER, eps_u=EPS)
+        opts = G.Options(P=P, generations=GENERATIONS, seed=SEED, init_max_iter=INIT_MAX_ITER)
+        bufs = G.pifcm3d_buffers(vol, prm, opts, nx=n)
+        G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(runs):
+            G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs, sync=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / runs
+        _, res = G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs)
+        # the same run captured once into a CUDA graph (pifcm3d never waits
+        # on the host, so all ~3800 launches go into one graph) and replayed
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+            G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs, sync=False)
+        graph.replay()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(runs):
+            graph.replay()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms_g = ev0.elapsed_time(ev1) / runs
+        _, res_g = G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs)
+        del graph
+        out.append({"n": n, "seconds_per_run": ms / 1e3, "updates": res["updates"],
+                    "value": res["updates"] / (ms / 1e3), "unit": UNIT,
+                    "graph": {"seconds_per_run": ms_g / 1e3,
+                              "value": res["updates"] / (ms_g / 1e3)},
+                    "lambda_xi": [res["lambda"], res["xi"]],
+                    "graph_result_equal": res_g == res})
+    return {"workload": SWEEP_WORKLOAD, "sizes": out}
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_sample_rate(raw, seconds_cap=30.0):
     """Updates/s of the FP64 oracle: IFCM iterations of one particle
@@ -702,6 +757,8 @@ def run_ours(args):
         line["precision"] = precision_leg(G, phantoms, dev)
     if rank == 0 and not args.skip_differentiation:
         line["differentiation"] = differentiation_leg(G, phantoms, dev)
+    if rank == 0 and not args.skip_sweep:
+        line["sweep2d"] = sweep_leg(G, phantoms, dev)
     if plain is not None:
         line["plain"] = plain
         line["plain"]["batched_over_plain"] = value / world / plain["value"]
@@ -728,6 +785,8 @@ def main():
                     help="leave out the uneven multi-volume batch")
     ap.add_argument("--skip-precision", action="store_true",
                     help="leave out the FP32 / bf16 membership storage comparison")
+    ap.add_argument("--skip-sweep", action="store_true",
+                    help="leave out the 2D size sweep (32^2 ... 854^2 slices)")
     ap.add_argument("--skip-differentiation", action="store_true",
                     help="leave out the gradient / polish leg")
     ap.add_argument("--small", action="store_true",
