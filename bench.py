@@ -134,22 +134,25 @@ def rank_seed(rank):
 
 
 def stencil_source_sha():
+    """Hash of the sources that generate the FP32 pair-word stencil kernel."""
     h = hashlib.sha256()
-    for name in ("stencil_kernel.cuh", "ifcm_stencil.cu", "ifcm_stencil_f32p_np2.cu",
-                 "ifcm_math.cuh", "common.cuh", "launch.h", "api.cu"):
+    for name in ("stencil_kernel.cuh", "ifcm_stencil_f32p_np2.cu", "ifcm_math.cuh", "common.cuh",
+                 "launch.h"):
         with open(os.path.join(ROOT, "paper_2002_01981_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def stencil_traffic_per_update():
+def stencil_traffic_per_update(plan_np, plan_tz):
     """DRAM bytes per update of the stencil kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and plan."""
     path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_source_sha") == stencil_source_sha():
+        pl = d.get("plan", {})
+        if (d.get("kernel_source_sha") == stencil_source_sha() and
+                pl.get("particles_per_item") == plan_np and pl.get("tz") == plan_tz):
             return float(d["dram_bytes_per_update"])
     except Exception:
         pass
@@ -725,7 +728,7 @@ def run_ours(args):
     bytes_per_update = 2 * C * 4 + 4.0 / plan_np
     per_launch_updates = stencil_updates_step * args.steps / max(kernel_launches, 1)
     achieved = (stencil_updates_step * args.steps * bytes_per_update) / (kernel_ms / 1e3) / 1e9
-    traffic_pu = stencil_traffic_per_update()
+    traffic_pu = stencil_traffic_per_update(plan_np, plan_tz)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic_pu * per_launch_updates if traffic_pu else None,

@@ -75,54 +75,6 @@ __device__ __forceinline__ float fast_rcp(float v) {
   return r;
 }
 
-// voxel_update with hardware reciprocals: d^2 >= dist_floor and S >= 1/c are
-// normal numbers, so each reciprocal is within 1 ulp.
-template <int C>
-__device__ __forceinline__ void voxel_update_fast(const float (&H)[C], const float (&F)[C],
-                                                  float xc, const float (&cc)[C],
-                                                  const MethodConsts& k, float (&u)[C],
-                                                  float (&um)[C], float& Jv) {
-  float d2[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const float fac = fmaxf(1.0f - k.lam * H[j] - k.xi * F[j], 0.0f);   // Eq 4
-    const float dd = xc - cc[j];
-    d2[j] = fmaxf(dd * dd * fac, k.dist_floor);
-  }
-  if (k.m_is_2) {
-    float r[C];
-    float S = 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      r[j] = fast_rcp(d2[j]);
-      S += r[j];
-    }
-    const float invS = fast_rcp(S);
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      u[j] = r[j] * invS;
-      um[j] = u[j] * u[j];
-    }
-    Jv = invS;
-  } else {
-    float aa[C];
-    float S = 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      aa[j] = exp2f(-k.inv_m1 * log2f(d2[j]));
-      S += aa[j];
-    }
-    const float invS = fast_rcp(S);
-    Jv = 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      u[j] = aa[j] * invS;
-      um[j] = exp2f(k.m * log2f(u[j]));
-      Jv += um[j] * d2[j];
-    }
-  }
-}
-
 // In-volume neighbour count and sum of q^2 = dx^2 + dy^2 + dz^2 (Eq 8,
 // reading R1) over the 3x3x3 box around (X, Y, Z), excluding the voxel itself
 // and every position outside the volume (reading R4).  With a_* in-volume
