@@ -534,6 +534,52 @@ def sweep_leg(G, phantoms, dev, runs=2):
 
 
 # ------------------------------------------------------------ CPU oracle
+def _oracle_particle_iteration(args):
+    """One FP64 oracle IFCM iteration of one particle on a slab (a worker of
+    the all-cores baseline): returns (seconds, voxels, J)."""
+    x, lam, xi = args
+    from oracle import ifcm as O
+    U = np.full((C,) + x.shape, 1.0 / C)
+    Cc = (np.arange(C) + 0.5) / C
+    t0 = time.perf_counter()
+    _, _, J, _ = O.ifcm_iteration(x, U, Cc, lam, xi)
+    return time.perf_counter() - t0, x.size, J
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_all_cores_rate(raw):
+    """Updates/s of the FP64 oracle over all host cores: one particle per
+    worker process (spawned: this process already holds a CUDA context),
+    one IFCM iteration each on the 48-plane slab, 2 rounds of one task per
+    core.  Timed from the first task's submission to the last result, after a
+    warm-up round that starts the workers."""
+    import multiprocessing as mp
+    from oracle import ifcm as O
+    cores = os.cpu_count() or 1
+    x = O.normalize(raw)[:CPU_SLAB]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_particle_iteration, [(x[:2], 0.5, 0.5)] * cores)      # start workers
+        tasks = [(x, 0.1 + 0.8 * (i % 7) / 7.0, 0.5) for i in range(2 * cores)]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_particle_iteration, tasks, chunksize=1)
+        el = time.perf_counter() - t0
+    assert all(np.isfinite(r[2]) for r in res)
+    return sum(r[1] for r in res) / el, cores, len(tasks), el, x.shape
+
+
 def oracle_sample_rate(raw, seconds_cap=30.0):
     """Updates/s of the FP64 oracle: IFCM iterations of one particle
     (lambda = xi = 0.5) on a 48-plane z-slab of the workload volume."""
@@ -769,7 +815,15 @@ def run_ours(args):
         rate, n, el, shp = oracle_sample_rate(raw)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} FP64 oracle IFCM iterations of one particle "
-                                          f"on a {shp[0]}x{shp[1]}x{shp[2]} z-slab, {el:.1f} s"}
+                                          f"on a {shp[0]}x{shp[1]}x{shp[2]} z-slab, {el:.1f} s",
+                                "cpu_model": cpu_model()}
+        if not args.skip_all_cores:
+            ra, cores, ntask, ela, shp = oracle_all_cores_rate(raw)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": ra, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{ntask} particles x one FP64 oracle IFCM iteration on the "
+                          f"{shp[0]}x{shp[1]}x{shp[2]} z-slab, one spawned worker per core, "
+                          f"{ela:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -788,6 +842,8 @@ def main():
                     help="leave out the uneven multi-volume batch")
     ap.add_argument("--skip-precision", action="store_true",
                     help="leave out the FP32 / bf16 membership storage comparison")
+    ap.add_argument("--skip-all-cores", action="store_true",
+                    help="leave out the all-cores timing of the CPU oracle")
     ap.add_argument("--skip-sweep", action="store_true",
                     help="leave out the 2D size sweep (32^2 ... 854^2 slices)")
     ap.add_argument("--skip-differentiation", action="store_true",
