@@ -509,21 +509,19 @@ def sweep_leg(G, phantoms, dev, runs=2):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / runs
         _, res = G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs)
-        # the same run captured once into a CUDA graph (pifcm3d never waits
-        # on the host, so all ~3800 launches go into one graph) and replayed
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, capture_error_mode="relaxed"):
-            G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs, sync=False)
-        graph.replay()
+        # the same run captured once into a CUDA graph (pifcm3d_graph: the
+        # ~3800 launches of a run in one graph) and replayed
+        graph = G.pifcm3d_graph(vol, prm, opts, nx=n, buffers=bufs)
+        graph.launch()
         torch.cuda.synchronize()
         ev0.record()
         for _ in range(runs):
-            graph.replay()
+            graph.launch()
         ev1.record()
         torch.cuda.synchronize()
         ms_g = ev0.elapsed_time(ev1) / runs
-        _, res_g = G.pifcm3d(vol, prm, opts, nx=n, buffers=bufs)
-        del graph
+        res_g = graph.result()
+        graph.close()
         out.append({"n": n, "seconds_per_run": ms / 1e3, "updates": res["updates"],
                     "value": res["updates"] / (ms / 1e3), "unit": UNIT,
                     "graph": {"seconds_per_run": ms_g / 1e3,
@@ -547,6 +545,13 @@ def _oracle_particle_iteration(args):
 
 
 def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:

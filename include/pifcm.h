@@ -305,6 +305,20 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
                     const pifcm_options* o, float* u_out, pifcm_result* result,
                     void* ws, size_t ws_bytes, void* stream);
 
+/* The same run captured once into a CUDA graph (the ifcm_graph type of
+ * pso_fitness_multi_graph).  pifcm3d never waits on the host, so its ~3800
+ * launches (181^3, 20 particles x 30 generations) become one graph; every
+ * ifcm_graph_launch re-runs Algorithm 1 on what vol then holds, with the
+ * same pointers, which must stay valid while the graph lives.  The stencil
+ * plans are fixed at capture (the tuning cache, else the built-in rule).
+ * Replays on one workspace must not overlap.  Checks as for pifcm3d;
+ * IFCM_ERR_CUDA when capture or instantiation fails.  Replaying saves the
+ * launch latency that bounds small images (about 8 ms of a 31 ms run at
+ * 32 x 32). */
+ifcm_status pifcm3d_graph(const float* vol, ifcm_shape shape, const ifcm_params* p,
+                          const pifcm_options* o, float* u_out, pifcm_result* result, void* ws,
+                          size_t ws_bytes, ifcm_graph* out);
+
 /* The same with HOST input and outputs: copies vol_host in, runs pifcm3d and
  * copies the memberships and the result block back, then synchronises the
  * stream.  The workspace also holds the device copies of the volume, the

@@ -1252,14 +1252,11 @@ struct ifcm_graph_t {
   cudaGraphExec_t exec;
 };
 
-extern "C" {
+namespace {
 
-ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
-                                    const ifcm_params* p, void* ws, size_t ws_bytes,
-                                    ifcm_graph* out) {
-  if (!out) return fail(IFCM_ERR_INVALID, "out is NULL");
-  *out = nullptr;
-  ST_TRY(check_multi(vols, n, p));
+// Captures body(stream) on a private stream into an instantiated graph.
+template <class Body>
+ifcm_status capture_graph(Body body, ifcm_graph* out) {
   cudaStream_t cs = nullptr;
   CU_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
@@ -1267,7 +1264,7 @@ ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
     cudaStreamDestroy(cs);
     return fail(IFCM_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
   }
-  const ifcm_status rc = pso_fitness_multi(vols, n, p, ws, ws_bytes, cs);
+  const ifcm_status rc = body(cs);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(cs);
@@ -1283,6 +1280,20 @@ ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
   }
   *out = new ifcm_graph_t{g, ex};
   return IFCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ifcm_status pso_fitness_multi_graph(const ifcm_batch_volume* vols, int32_t n,
+                                    const ifcm_params* p, void* ws, size_t ws_bytes,
+                                    ifcm_graph* out) {
+  if (!out) return fail(IFCM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  ST_TRY(check_multi(vols, n, p));
+  return capture_graph(
+      [&](cudaStream_t cs) { return pso_fitness_multi(vols, n, p, ws, ws_bytes, cs); }, out);
 }
 
 ifcm_status ifcm_graph_launch(ifcm_graph g, void* stream) {
@@ -1403,6 +1414,18 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
                        b.iters_init, b.updates, b.best, b.status, result, st));
   return IFCM_OK;
+}
+
+ifcm_status pifcm3d_graph(const float* vol, ifcm_shape shape, const ifcm_params* p,
+                          const pifcm_options* o, float* u_out, pifcm_result* result, void* ws,
+                          size_t ws_bytes, ifcm_graph* out) {
+  if (!out) return fail(IFCM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  return capture_graph(
+      [&](cudaStream_t cs) {
+        return pifcm3d(vol, shape, p, o, u_out, result, ws, ws_bytes, cs);
+      },
+      out);
 }
 
 size_t pifcm3d_host_workspace_bytes(ifcm_shape shape, const ifcm_params* p,

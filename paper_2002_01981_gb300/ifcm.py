@@ -462,6 +462,52 @@ def pifcm3d(vol, params, options, nx=None, buffers=None, sync=True):
     return u_out, _result_dict(r, params.c)
 
 
+class RunGraph:
+    """A captured pifcm3d run: ``launch()`` replays Algorithm 1 on what the
+    volume tensor then holds; ``result()`` reads the result block of the last
+    replay (synchronising)."""
+
+    def __init__(self, handle, buffers, keep, c):
+        self._h = handle
+        self.u_out, self._res, self.ws = buffers
+        self._keep = keep
+        self._c = c
+
+    def launch(self):
+        N.check(N.load().ifcm_graph_launch(self._h, _stream()))
+
+    def result(self):
+        r = N.PifcmResult.from_buffer_copy(self._res.cpu().numpy().tobytes())
+        if r.status:
+            N.check(device_status(self.ws))
+        return _result_dict(r, self._c)
+
+    def close(self):
+        if self._h:
+            N.load().ifcm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pifcm3d_graph(vol, params, options, nx=None, buffers=None):
+    """Capture one pifcm3d run into a CUDA graph (replayed by RunGraph.launch)."""
+    lib = N.load()
+    _check_cuda(vol, torch.float32, "vol")
+    shp = shape_of(vol, nx)
+    p, o = params.native(), options.native()
+    bufs = buffers if buffers is not None else pifcm3d_buffers(vol, params, options, nx)
+    u_out, res, ws = bufs
+    h = ctypes.c_void_p()
+    N.check(lib.pifcm3d_graph(_ptr(vol), shp, ctypes.byref(p), ctypes.byref(o), _ptr(u_out),
+                              _ptr(res), _ptr(ws), ws.numel(), ctypes.byref(h)))
+    return RunGraph(h, bufs, vol, params.c)
+
+
 def pifcm3d_host_workspace(shape, params, options, device="cuda"):
     lib = N.load()
     p, o = params.native(), options.native()

@@ -101,6 +101,8 @@ SIGNATURES = {
                                            POINTER(PifcmOptions)]),
     "pifcm3d": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), POINTER(PifcmOptions),
                           c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pifcm3d_graph": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams), POINTER(PifcmOptions),
+                                c_void_p, c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
     "pifcm3d_host_workspace_bytes": (c_size_t, [IfcmShape, POINTER(IfcmParams),
                                                 POINTER(PifcmOptions)]),
     "pifcm3d_host": (c_int32, [c_void_p, IfcmShape, POINTER(IfcmParams),

@@ -333,6 +333,26 @@ def test_split_swarm_on_one_rank_equals_pifcm3d(G, slice_z):
     assert torch.equal(Ua[..., :22], Ub[..., :22])
 
 
+def test_pifcm3d_graph_replays_equal_direct_runs(G):
+    raw = phantoms.brain_phantom((7, 18, 21), seed=13, sigma=0.05)
+    prm = G.Params(c=4, max_iter=6, eps_u=1e-5)
+    opts = G.Options(P=4, generations=3, seed=6, init_max_iter=30)
+    vol = dev_vol(raw)
+    Ud, rd = G.pifcm3d(vol, prm, opts, nx=21)
+    graph = G.pifcm3d_graph(vol, prm, opts, nx=21)
+    for _ in range(2):
+        graph.launch()
+        rg = graph.result()
+        assert rg == rd
+        assert torch.equal(graph.u_out[..., :21], Ud[..., :21])
+    # a replay follows the buffer's new contents
+    vol.copy_(dev_vol(phantoms.brain_phantom((7, 18, 21), seed=14, sigma=0.05)))
+    graph.launch()
+    _, rd2 = G.pifcm3d(vol, prm, opts, nx=21)
+    assert graph.result() == rd2 and rd2 != rd
+    graph.close()
+
+
 def test_pifcm3d_slice_mode(G):
     raw = phantoms.brain_phantom((6, 20, 22), seed=8)
     prm = G.Params(c=3, max_iter=5, eps_u=0.0)
