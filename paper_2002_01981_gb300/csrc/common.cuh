@@ -59,6 +59,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of one phase of an mbarrier (acquire): true once the
+// phase has completed.  Unlike try_wait it never suspends the thread, so it
+// can be issued well before its result is needed.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait on one phase of an mbarrier.  Each try_wait suspends the
 // thread for a hardware-chosen interval; after `limit` unsuccessful tries the
 // wait gives up and returns false so that the caller can record

@@ -3,14 +3,14 @@
 // for every active particle of a batch, in one persistent launch.
 //
 // Work item = (group of NP particles, TX x TY column tile, z-chunk of tz
-// planes).  Warp 8 of each CTA is the producer: one lane walks the CTA's items
-// plane by plane and, for each plane, issues TMA tile loads of the normalised
-// volume x and of the c membership planes U^t of each particle of the group
-// (one-voxel halo in y, aligned four-voxel margins in x) into a ring of
-// shared-memory stages, gated by "full" (transaction bytes) and "empty"
-// (one arrival per consumer warp) mbarriers.  Warps 0-7 are consumers: thread
-// (tx, ty) owns column (x0 + tx, y0 + ty) and keeps four centres of the column
-// in registers.  The plane being consumed contributes to the centre below it
+// planes).  The last warp of each CTA (warp TY) is the producer: one lane
+// walks the CTA's items plane by plane and, for each plane, issues TMA tile
+// loads of the normalised volume x and of the c membership planes U^t of each
+// particle of the group (one-voxel halo in y, aligned four-voxel margins in x)
+// into a ring of shared-memory stages, gated by "full" (transaction bytes) and
+// "empty" (one arrival per consumer warp) mbarriers.  Warps 0 .. TY-1 are
+// consumers: thread (tx, ty) owns column (x0 + tx, y0 + ty) and keeps four
+// centres of the column in registers.  The plane being consumed contributes to the centre below it
 // (dz = +1), its own centre (dz = 0) and the centre above (dz = -1); the
 // centre two planes below, completed by the previous plane, is finalised in
 // the same step so that its long dependency chain overlaps the stencil
@@ -20,6 +20,20 @@
 // H = sum u g / sum g, F = sum u^2 q^2 / sum q^2 (q^2 = dx^2+dy^2+dz^2,
 // reading R1), Eqs 4 and 2, U^{t+1} written from registers, and the centre's
 // shares of sum u^m, sum u^m x, J and max|du|.
+//
+// Keeping the consumers' plane step free of stalls and branches decides the
+// speed, since the kernel is bound by instruction issue and latency:
+// - each stage's full barrier is tested once, without blocking, a plane
+//   before the stage is needed; a blocking (bounded) wait follows only when
+//   the stage had not landed by then;
+// - the finalisation takes a branch-free form whenever every lane of the
+//   warp allows it (a 3D centre off the z faces, sum g >= 1e-30, m = 2; Q of
+//   the column computed once per item; lanes outside the volume masked), so
+//   that it and the plane's stencil form one basic block the compiler can
+//   interleave.  Every other centre takes the general form, with the same
+//   arithmetic;
+// - U^{t+1} goes out through explicit global stores, which the compiler can
+//   move shared-memory loads across.
 //
 // Neighbours outside the volume are excluded (reading R4) without masks:
 // the volume's tensor map fills positions outside the volume with NaN and
@@ -69,7 +83,8 @@ constexpr int PLANE = BX * BY;         // floats in one channel of a stage
 #define PIFCM_STENCIL_STAGES 8
 #endif
 constexpr int NSTAGE = PIFCM_STENCIL_STAGES;   // ring depth
-static_assert(NSTAGE >= 5, "the consumers hold four stages at a time (pz-2 .. pz+1)");
+static_assert(NSTAGE >= 6,
+              "the consumers hold five stages at a time (pz-2 .. pz+1, and pz+2 tested)");
 constexpr int XBYTES = ((PLANE * 4 + 127) / 128) * 128;
 constexpr int CBAR = 1;                // named barrier id of the consumer warps
 
@@ -340,21 +355,21 @@ struct Ctx {
   int X, Y;
   bool col_ok, col_interior;
   int col_off;                 // Y * pitch + X
+  float invQ_col;              // 1 / Q of the column's centres off the z faces (Eq 8)
 };
 
 __device__ __forceinline__ float2 max2(float2 v, float lo) {
   return make_float2(fmaxf(v.x, lo), fmaxf(v.y, lo));
 }
 
-// Finalise one centre (its u^t is read from its plane's stage at cus): H and F
-// (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
-// the centre's shares of Eqs 1 and 3, in packed pairs.
+// H and F of a centre in the general case (Eqs 5-8): Q from the in-volume
+// neighbours when the centre is on a face, and the small or zero sum_k g_ik
+// cases of readings R2 and R3.
 template <int C, int NP, int UL>
-__device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
-                                                int cidx, float xc, int z, bool interior,
-                                                const VolDesc& a, const Item& it,
-                                                const ItemConst<C, NP>& ic, const Ctx& cx,
-                                                const MethodConsts& k, Sums<C, NP>& acc) {
+__device__ __forceinline__ void neighbour_terms(const Slot<C, NP>& sl, int z, bool interior,
+                                                const VolDesc& a, const Item& it, const Ctx& cx,
+                                                float2 (&H)[Pairs<C, NP>::K],
+                                                float2 (&F)[Pairs<C, NP>::K]) {
   constexpr int K = Pairs<C, NP>::K;
   float invQ;
   int cnt = 1;
@@ -365,7 +380,6 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
     box_counts(cx.X, cx.Y, z, a.nx, a.ny, a.nz, cnt, Q);
     invQ = cnt > 0 ? __frcp_rn(Q) : 0.0f;
   }
-  float2 H[K], F[K];
   if (cnt == 0) {
 #pragma unroll
     for (int q = 0; q < K; ++q) H[q] = F[q] = make_float2(0.0f, 0.0f);
@@ -414,6 +428,40 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       }
     }
   }
+}
+
+// Finalise one centre (its u^t is read from its plane's stage at cus): H and F
+// (Eqs 5, 7), then Eq 4 (clamped factor, floored d^2, reading R2), Eq 2, and
+// the centre's shares of Eqs 1 and 3, in packed pairs.  FAST is the common
+// case, taken only when the caller has checked it for every lane of the warp:
+// a centre of a 3D volume off its z faces (Q depends on the column alone and
+// was computed once per item), sum_k g_ik >= 1e-30 and m = 2.
+// It has no branch, so that the compiler can schedule it in one basic block
+// with the next plane's stencil; its arithmetic is the general path's.  With
+// MASK, lanes whose column lies outside the volume (live = false) compute on
+// but store nothing and add nothing to the sums.
+template <int C, int NP, int UL, bool FAST, bool MASK = false>
+__device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const float* cus,
+                                                int cidx, float xc, int z, bool interior,
+                                                const VolDesc& a, const Item& it,
+                                                const ItemConst<C, NP>& ic, const Ctx& cx,
+                                                const MethodConsts& k, Sums<C, NP>& acc,
+                                                bool live = true) {
+  constexpr int K = Pairs<C, NP>::K;
+  const bool keep = !MASK || live;
+  if (MASK) xc = keep ? xc : 0.0f;    // x is NaN outside the volume
+  float2 H[K], F[K];
+  if (FAST) {
+    const float2 iq = dup2(cx.invQ_col);
+    const float2 ig = dup2(fast_rcp(sl.G));
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      F[q] = __fmul2_rn(sl.F[q], iq);
+      H[q] = __fmul2_rn(sl.H[q], ig);
+    }
+  } else {
+    neighbour_terms<C, NP, UL>(sl, z, interior, a, it, cx, H, F);
+  }
   // Eq 4 with reading R2: d2 = max(D max(f, 0), floor) = max(D f, floor) for
   // D >= 0 and floor > 0, so the factor needs no clamp of its own
   const float2 one2 = dup2(1.0f), xc2 = dup2(xc);
@@ -426,7 +474,7 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
   // Eq 2
   float2 u[K], um[K];
-  if (k.m_is_2) {
+  if (FAST || k.m_is_2) {
     float2 r[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) r[q] = make_float2(fast_rcp(d2[q].x), fast_rcp(d2[q].y));
@@ -436,19 +484,20 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
 #pragma unroll
       for (int q = 1; q < K; ++q) S = __fadd2_rn(S, r[q]);
       inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
-      acc.J[0] += inv.x;                       // sum_j u_j^2 d2_j = 1/S
-      acc.J[NP - 1] += inv.y;
+      acc.J[0] += keep ? inv.x : 0.0f;         // sum_j u_j^2 d2_j = 1/S
+      acc.J[NP - 1] += keep ? inv.y : 0.0f;
     } else {
       float S = 0.0f;
 #pragma unroll
       for (int q = 0; q < K; ++q) S += (2 * q + 1 < C) ? r[q].x + r[q].y : r[q].x;
       inv = dup2(fast_rcp(S));
-      acc.J[0] += inv.x;
+      acc.J[0] += keep ? inv.x : 0.0f;
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       u[q] = __fmul2_rn(r[q], inv);
       um[q] = __fmul2_rn(u[q], u[q]);
+      if (MASK) um[q] = keep ? um[q] : make_float2(0.0f, 0.0f);
     }
   } else {
     float Sp[NP];
@@ -500,9 +549,9 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
     for (int q = 0; q < K; ++q) {
       const bool pad_hi = NP == 1 && 2 * q + 1 >= C;
       const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
-      dst[q * plane + voff] = uq;
+      if (keep) __stcg(&dst[q * plane + voff], uq);
       const float2 e = __ffma2_rn(cw[q * PLANE + cidx], dup2(-1.0f), uq);   // u' - u
-      const float e0 = fabsf(e.x), e1 = fabsf(e.y);
+      const float e0 = keep ? fabsf(e.x) : 0.0f, e1 = keep ? fabsf(e.y) : 0.0f;
       if (NP == 2) {
         acc.dm[0] = fmaxf(acc.dm[0], e0);
         acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
@@ -523,10 +572,10 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
       const bool pad_hi = NP == 1 && 2 * q + 1 >= C;
       const float2 uq = pad_hi ? make_float2(u[q].x, 0.0f) : u[q];
       const uint32_t w = pack_bf16x2(uq);
-      dst[q * plane + voff] = w;
+      if (keep) __stcg(&dst[q * plane + voff], w);
       const float2 e = __ffma2_rn(unpack_bf16x2(cw[q * PLANE + cidx]), dup2(-1.0f),
                                   unpack_bf16x2(w));                       // u' - u
-      const float e0 = fabsf(e.x), e1 = fabsf(e.y);
+      const float e0 = keep ? fabsf(e.x) : 0.0f, e1 = keep ? fabsf(e.y) : 0.0f;
       if (NP == 2) {
         acc.dm[0] = fmaxf(acc.dm[0], e0);
         acc.dm[NP - 1] = fmaxf(acc.dm[NP - 1], e1);
@@ -542,8 +591,9 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const float uj = pick<C, NP>(u, p, j);
-      ic.dst[p][j * plane + voff] = uj;
-      acc.dm[p] = fmaxf(acc.dm[p], fabsf(uj - cus[p * ufloats<C>() + j * PLANE + cidx]));
+      if (keep) __stcg(&ic.dst[p][j * plane + voff], uj);
+      const float ej = fabsf(uj - cus[p * ufloats<C>() + j * PLANE + cidx]);
+      acc.dm[p] = fmaxf(acc.dm[p], keep ? ej : 0.0f);
     }
   }
 }
@@ -684,6 +734,14 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     cx.col_ok = (cx.X < vd.nx) && (cx.Y < vd.ny);
     cx.col_interior = cx.X > 0 && cx.X < vd.nx - 1 && cx.Y > 0 && cx.Y < vd.ny - 1;
     cx.col_off = cx.Y * vd.pitch + cx.X;
+    const bool warp_all_live = __all_sync(0xffffffffu, cx.col_ok);
+    const bool warp_any_live = __any_sync(0xffffffffu, cx.col_ok);
+    {   // Q of the column's centres with both z neighbours in the volume
+      int cnt;
+      float Q;
+      box_counts(cx.X, cx.Y, 1, vd.nx, vd.ny, 3, cnt, Q);
+      cx.invQ_col = cx.col_interior ? (1.0f / 54.0f) : __frcp_rn(Q);
+    }
     if (tid == 0) {
       float lam[2], xi[2], cc[2][C];
 #pragma unroll
@@ -722,30 +780,57 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1 while
     // plane pz is consumed.  The centre completed by plane pz - 1 is finalised
     // in the same basic block as plane pz's stencil so that its dependency
-    // chain (Eqs 4 and 2) overlaps the stencil arithmetic.
+    // chain (Eqs 4 and 2) overlaps the stencil arithmetic.  Each stage is
+    // waited for once and one plane early: plane pz consumes stages pz - 2 ..
+    // pz + 1 (pz + 1 supplies x of the centre above), and the full barrier of
+    // stage pz + 2 is tested without blocking when plane pz starts, its result
+    // read only after plane pz's arithmetic; only a stage that had not landed
+    // by then is waited for (bounded).
+    bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
     for (int kk = 0; kk < np; ++kk) {
       const int qq = q0 + kk;
       const int pz = it.pzb + kk;
       const bool has_next = kk + 1 < np;
-      const bool ok = wait_full(qq) && (!has_next || wait_full(qq + 1));
+      const bool need2 = kk + 2 < np;
+      const bool landed2 =
+          !need2 || mbar_test_wait(&full[(qq + 2) % NSTAGE],
+                                   static_cast<uint32_t>(((qq + 2) / NSTAGE) & 1));
+      // centre pz - 2 is finalised here when it lies in the item's z-range;
+      // the whole warp takes the fast form when every lane can (voted by all
+      // 32 lanes, before any lane may skip the plane)
+      const int zd = pz - 2;
+      const bool fin_z = kk >= 2 && zd >= it.z0 && zd < it.z1;
+      const bool fin = fin_z && cx.col_ok;
+      const bool zin = zd > 0 && zd < vd.nz - 1;
+      const bool inter = cx.col_interior && zin;
+      const bool all_g = __all_sync(0xffffffffu, !cx.col_ok || sd.G >= 1.0e-30f);
+      const bool fast = fin_z && zin && all_g && z3 && k.m_is_2 && warp_any_live;
       if (ok) {
         const float* xs = xs_of(qq % NSTAGE);
         const float* us = us_of(qq % NSTAGE);
         const float x_mid = xs[cidx];
         const float x_lo = kk > 0 ? xs_of((qq + NSTAGE - 1) % NSTAGE)[cidx] : 0.0f;
         const float x_hi = has_next ? xs_of((qq + 1) % NSTAGE)[cidx] : 0.0f;
-        const int zd = pz - 2;
-        if (kk >= 2 && zd >= it.z0 && zd < it.z1 && cx.col_ok) {
-          const int sdi = (qq + NSTAGE - 2) % NSTAGE;
-          finalize_centre<C, NP, UL>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
-                                 cx.col_interior && zd > 0 && zd < vd.nz - 1, vd, it, s_ic, cx,
-                                 k, acc);
-        }
-        if (z3)
+        const int sdi = (qq + NSTAGE - 2) % NSTAGE;
+        if (fast && warp_all_live) {
+          finalize_centre<C, NP, UL, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, true, vd,
+                                           it, s_ic, cx, k, acc);
           accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-        else
-          accumulate_plane<C, NP, UL, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+        } else if (fast) {      // a tile overhanging the volume: some lanes outside
+          finalize_centre<C, NP, UL, true, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
+                                                 true, vd, it, s_ic, cx, k, acc, cx.col_ok);
+          accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+        } else {
+          if (fin)
+            finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, inter,
+                                              vd, it, s_ic, cx, k, acc);
+          if (z3)
+            accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          else
+            accumulate_plane<C, NP, UL, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+        }
       }
+      if (!landed2) ok = ok && wait_full(qq + 2);
       if (kk >= 2) release(qq - 2);
       sd = sl;
       sl = sm;
@@ -759,13 +844,13 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
       if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
         const int sdi = (ql + NSTAGE - 1) % NSTAGE;
-        finalize_centre<C, NP, UL>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
+        finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
                                cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
                                it, s_ic, cx, k, acc);
       }
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
         const int sli = ql % NSTAGE;
-        finalize_centre<C, NP, UL>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
+        finalize_centre<C, NP, UL, false>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
                                cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
       }
       if (np >= 2) release(ql - 1);
