@@ -787,7 +787,10 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     // read only after plane pz's arithmetic; only a stage that had not landed
     // by then is waited for (bounded).
     bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
-    for (int kk = 0; kk < np; ++kk) {
+    // One plane: finalise centre pz - 2 (slot sd), add plane pz to the centres
+    // pz - 1, pz and pz + 1 (slots sl, sm and sh; sh starts cleared).
+    auto step = [&](int kk, Slot<C, NP>& sd, Slot<C, NP>& sl, Slot<C, NP>& sm,
+                    Slot<C, NP>& sh) {
       const int qq = q0 + kk;
       const int pz = it.pzb + kk;
       const bool has_next = kk + 1 < np;
@@ -832,6 +835,9 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       }
       if (!landed2) ok = ok && wait_full(qq + 2);
       if (kk >= 2) release(qq - 2);
+    };
+    for (int kk = 0; kk < np; ++kk) {
+      step(kk, sd, sl, sm, sh);
       sd = sl;
       sl = sm;
       sm = sh;
