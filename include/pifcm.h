@@ -208,11 +208,13 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
  * Work decomposition of the batched stencil launches (no arithmetic change
  * beyond the order of the FP64 partial sums).  A launch is cut into work
  * items of np particles (1, or 2 for c <= 4) x a 32-column tile x a z-chunk
- * of tz planes.  Mode 0 (default): a built-in rule picks the deepest chunks
- * that still give every CTA four items.  Mode 1: the first run of each
- * (membership type, c, volume extents, particle counts) times the candidate
- * plans on its own buffers (a host synchronisation; never on a stream being
- * captured into a graph) and the fastest is cached for the process.
+ * of tz planes (in a 2D image: a run of tz tiles down the image, the tiles
+ * taking the place of the planes).  Mode 0 (default): a built-in rule picks
+ * the deepest chunks that still give every CTA four items.  Mode 1: the first
+ * run of each (membership type, c, volume extents, particle counts) times the
+ * candidate plans on its own buffers (a host synchronisation; never on a
+ * stream being captured into a graph) and the fastest is cached for the
+ * process.
  * Thread-safe.
  */
 void ifcm_autotune_enable(int32_t mode);

@@ -127,26 +127,43 @@ struct Tiling {
   int tiles_x, tiles_y, zchunks, tz, n_tiles;
 };
 
-// A work item covers ceil(nz / chunks) planes of one 32 x kTY column tile.
-// Chunks never get shorter than kMinTileZ planes (unless the volume is), so
-// a particle never has more than max_chunks(nz) x tiles_xy records.
+// A work item covers ceil(nz / chunks) planes of one 32 x kTY column tile,
+// with at most ceil(nz / kMinTileZ) chunks.  In a 2D image (nz = 1) an item is
+// instead a run of 32 x kTY tiles down the image, one tile per ring stage:
+// chunks cut each column of tiles into runs of ceil(y-tiles / chunks) tiles.
+// The planning rule keeps those runs near kMinTileRun tiles or longer, but
+// tiling() accepts any cut, down to one tile per item (the cut of images too
+// small to fill the GPU).
 constexpr int kMinTileZ = 8;
+constexpr int kMinTileRun = 4;
 
-int max_chunks(int nz) { return nz <= kMinTileZ ? 1 : (nz + kMinTileZ - 1) / kMinTileZ; }
+int y_tiles(const ifcm_shape& s) { return (s.ny + kTY - 1) / kTY; }
+
+// Steps of a whole item column: planes in 3D, tiles down the image in 2D.
+int column_depth(const ifcm_shape& s) { return s.nz == 1 ? y_tiles(s) : s.nz; }
+
+int max_chunks(const ifcm_shape& s) {
+  const int d = column_depth(s), m = s.nz == 1 ? kMinTileRun : kMinTileZ;
+  return d <= m ? 1 : (d + m - 1) / m;
+}
+
+// Most chunks tiling() accepts.
+int chunk_limit(const ifcm_shape& s) { return s.nz == 1 ? column_depth(s) : max_chunks(s); }
 
 Tiling tiling(const ifcm_shape& s, int chunks) {
   Tiling t;
   t.tiles_x = (s.nx + kTX - 1) / kTX;
-  t.tiles_y = (s.ny + kTY - 1) / kTY;
-  const int k = chunks < 1 ? 1 : (chunks > max_chunks(s.nz) ? max_chunks(s.nz) : chunks);
-  t.tz = (s.nz + k - 1) / k;
-  t.zchunks = (s.nz + t.tz - 1) / t.tz;
+  t.tiles_y = s.nz == 1 ? 1 : y_tiles(s);
+  const int d = column_depth(s), mk = chunk_limit(s);
+  const int k = chunks < 1 ? 1 : (chunks > mk ? mk : chunks);
+  t.tz = (d + k - 1) / k;
+  t.zchunks = (d + t.tz - 1) / t.tz;
   t.n_tiles = t.tiles_x * t.tiles_y * t.zchunks;
   return t;
 }
 
 // Most records one particle of this volume can have (any plan).
-int max_tiles(const ifcm_shape& s) { return tiling(s, max_chunks(s.nz)).n_tiles; }
+int max_tiles(const ifcm_shape& s) { return tiling(s, chunk_limit(s)).n_tiles; }
 
 constexpr int kPlainVpt = 32;
 
@@ -387,7 +404,7 @@ int plan_grid(int c, int layout, const StencilPlan& pl, long long items) {
 int most_chunks(const BatchVol* vols, int n) {
   int k = 1;
   for (int v = 0; v < n; ++v)
-    if (max_chunks(vols[v].shape.nz) > k) k = max_chunks(vols[v].shape.nz);
+    if (max_chunks(vols[v].shape) > k) k = max_chunks(vols[v].shape);
   return k;
 }
 
@@ -400,9 +417,19 @@ StencilPlan heuristic_plan(const BatchVol* vols, int n, int c, int layout) {
   // one particle: its clusters in pairs (two particles per item would
   // compute a duplicate lane)
   StencilPlan pl{P_total == 1 ? 1 : stencil_default_np(c), 1};
-  const long long want = 4LL * sm_count() * stencil_blocks_per_sm(c, pl.np, layout);
+  const long long grid =
+      static_cast<long long>(sm_count()) * stencil_blocks_per_sm(c, pl.np, layout);
   const int kmax = most_chunks(vols, n);
-  while (pl.chunks < kmax && plan_items(vols, n, pl) < want) ++pl.chunks;
+  while (pl.chunks < kmax && plan_items(vols, n, pl) < 4 * grid) ++pl.chunks;
+  // 2D images whose one-tile items would not even fill the grid: a launch is
+  // then one round of items, bound by its latency, so the shortest runs win
+  int depth = 1;
+  for (int v = 0; v < n; ++v) {
+    if (vols[v].shape.nz != 1) return pl;
+    if (column_depth(vols[v].shape) > depth) depth = column_depth(vols[v].shape);
+  }
+  const StencilPlan one{pl.np, depth};
+  if (plan_items(vols, n, one) <= grid) return one;
   return pl;
 }
 

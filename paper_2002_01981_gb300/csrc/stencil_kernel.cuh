@@ -3,7 +3,8 @@
 // for every active particle of a batch, in one persistent launch.
 //
 // Work item = (group of NP particles, TX x TY column tile, z-chunk of tz
-// planes).  The last warp of each CTA (warp TY) is the producer: one lane
+// planes); in a 2D image (group, column of tiles, run of tz tiles down the
+// image), the tiles taking the place of the planes.  The last warp of each CTA (warp TY) is the producer: one lane
 // walks the CTA's items plane by plane and, for each plane, issues TMA tile
 // loads of the normalised volume x and of the c membership planes U^t of each
 // particle of the group (one-voxel halo in y, aligned four-voxel margins in x)
@@ -209,9 +210,15 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTabl
   it.x0 = tx * TX;
   it.y0 = ty * TY;
   it.z0 = zc * vd.tz;
-  it.z1 = min(it.z0 + vd.tz, vd.nz);
-  it.pzb = max(it.z0 - 1, 0);
-  it.pze = min(it.z1, vd.nz - 1);
+  if (vd.nz == 1) {   // 2D: steps z0 .. z1 - 1 are tiles down the image (rows 11 z ..)
+    it.z1 = min(it.z0 + vd.tz, (vd.ny + TY - 1) / TY);
+    it.pzb = it.z0;
+    it.pze = it.z1 - 1;
+  } else {
+    it.z1 = min(it.z0 + vd.tz, vd.nz);
+    it.pzb = max(it.z0 - 1, 0);
+    it.pze = min(it.z1, vd.nz - 1);
+  }
   return it;
 }
 
@@ -357,6 +364,28 @@ struct Ctx {
   int col_off;                 // Y * pitch + X
   float invQ_col;              // 1 / Q of the column's centres off the z faces (Eq 8)
 };
+
+// The position of a consumer thread's column (X, Y) in a volume; Q of its
+// centres off the z faces (3D) or of its one centre (2D) comes from the
+// in-volume neighbour count, 54 or 12 in the interior (Eq 8, reading R4).
+__device__ __forceinline__ Ctx column_ctx(int X, int Y, const VolDesc& vd) {
+  Ctx cx;
+  cx.X = X;
+  cx.Y = Y;
+  cx.col_ok = (X < vd.nx) && (Y < vd.ny);
+  cx.col_interior = X > 0 && X < vd.nx - 1 && Y > 0 && Y < vd.ny - 1;
+  cx.col_off = Y * vd.pitch + X;
+  const bool z3 = vd.nz > 1;
+  if (cx.col_interior) {
+    cx.invQ_col = z3 ? (1.0f / 54.0f) : (1.0f / 12.0f);
+  } else {
+    int cnt;
+    float Q;
+    box_counts(X, Y, z3 ? 1 : 0, vd.nx, vd.ny, z3 ? 3 : 1, cnt, Q);
+    cx.invQ_col = cnt > 0 ? __frcp_rn(Q) : 0.0f;
+  }
+  return cx;
+}
 
 __device__ __forceinline__ float2 max2(float2 v, float lo) {
   return make_float2(fmaxf(v.x, lo), fmaxf(v.y, lo));
@@ -684,12 +713,15 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
             return;
           }
           if (*reinterpret_cast<volatile int*>(&s_abort)) return;
+          // a plane of the tile's column, or in 2D the tile of step pz
+          const int ty0 = vd.nz == 1 ? pz * TY : it.y0;
+          const int tz0 = vd.nz == 1 ? 0 : pz;
           mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP, UL>());
-          tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
-          tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
+          tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, ty0 - 1, tz0);
+          tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, ty0 - 1, tz0,
                       (paired(UL) ? it.unit : it.p0) * vd.src_cstride);
           if (NP == 2 && !paired(UL))
-            tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
+            tma_load_4d(us_of(s) + ufloats<C>(), mu, &full[s], it.x0 - 4, ty0 - 1, tz0,
                         it.p1 * vd.src_cstride);
         }
       }
@@ -728,20 +760,10 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     const VolDesc& vd = a.vol[it.v];
     const bool z3 = vd.nz > 1;
     const int plane = vd.nz * vd.ny * vd.pitch;
-    Ctx cx;
-    cx.X = it.x0 + tx;
-    cx.Y = it.y0 + ty;
-    cx.col_ok = (cx.X < vd.nx) && (cx.Y < vd.ny);
-    cx.col_interior = cx.X > 0 && cx.X < vd.nx - 1 && cx.Y > 0 && cx.Y < vd.ny - 1;
-    cx.col_off = cx.Y * vd.pitch + cx.X;
+    // the thread's column (in 2D: its column in the item's first tile)
+    const Ctx cx = column_ctx(it.x0 + tx, it.y0 + ty, vd);
     const bool warp_all_live = __all_sync(0xffffffffu, cx.col_ok);
     const bool warp_any_live = __any_sync(0xffffffffu, cx.col_ok);
-    {   // Q of the column's centres with both z neighbours in the volume
-      int cnt;
-      float Q;
-      box_counts(cx.X, cx.Y, 1, vd.nx, vd.ny, 3, cnt, Q);
-      cx.invQ_col = cx.col_interior ? (1.0f / 54.0f) : __frcp_rn(Q);
-    }
     if (tid == 0) {
       float lam[2], xi[2], cc[2][C];
 #pragma unroll
@@ -777,90 +799,142 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     const int np = it.pze - it.pzb + 1;
     const int q0 = q;
 
-    // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1 while
-    // plane pz is consumed.  The centre completed by plane pz - 1 is finalised
-    // in the same basic block as plane pz's stencil so that its dependency
-    // chain (Eqs 4 and 2) overlaps the stencil arithmetic.  Each stage is
-    // waited for once and one plane early: plane pz consumes stages pz - 2 ..
-    // pz + 1 (pz + 1 supplies x of the centre above), and the full barrier of
-    // stage pz + 2 is tested without blocking when plane pz starts, its result
-    // read only after plane pz's arithmetic; only a stage that had not landed
-    // by then is waited for (bounded).
-    bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
-    // One plane: finalise centre pz - 2 (slot sd), add plane pz to the centres
-    // pz - 1, pz and pz + 1 (slots sl, sm and sh; sh starts cleared).
-    auto step = [&](int kk, Slot<C, NP>& sd, Slot<C, NP>& sl, Slot<C, NP>& sm,
-                    Slot<C, NP>& sh) {
-      const int qq = q0 + kk;
-      const int pz = it.pzb + kk;
-      const bool has_next = kk + 1 < np;
-      const bool need2 = kk + 2 < np;
-      const bool landed2 =
-          !need2 || mbar_test_wait(&full[(qq + 2) % NSTAGE],
-                                   static_cast<uint32_t>(((qq + 2) / NSTAGE) & 1));
-      // centre pz - 2 is finalised here when it lies in the item's z-range;
-      // the whole warp takes the fast form when every lane can (voted by all
-      // 32 lanes, before any lane may skip the plane)
-      const int zd = pz - 2;
-      const bool fin_z = kk >= 2 && zd >= it.z0 && zd < it.z1;
-      const bool fin = fin_z && cx.col_ok;
-      const bool zin = zd > 0 && zd < vd.nz - 1;
-      const bool inter = cx.col_interior && zin;
-      const bool all_g = __all_sync(0xffffffffu, !cx.col_ok || sd.G >= 1.0e-30f);
-      const bool fast = fin_z && zin && all_g && z3 && k.m_is_2 && warp_any_live;
-      if (ok) {
-        const float* xs = xs_of(qq % NSTAGE);
-        const float* us = us_of(qq % NSTAGE);
-        const float x_mid = xs[cidx];
-        const float x_lo = kk > 0 ? xs_of((qq + NSTAGE - 1) % NSTAGE)[cidx] : 0.0f;
-        const float x_hi = has_next ? xs_of((qq + 1) % NSTAGE)[cidx] : 0.0f;
-        const int sdi = (qq + NSTAGE - 2) % NSTAGE;
-        if (fast && warp_all_live) {
-          finalize_centre<C, NP, UL, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, true, vd,
-                                           it, s_ic, cx, k, acc);
-          accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-        } else if (fast) {      // a tile overhanging the volume: some lanes outside
-          finalize_centre<C, NP, UL, true, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
-                                                 true, vd, it, s_ic, cx, k, acc, cx.col_ok);
-          accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-        } else {
-          if (fin)
-            finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, inter,
-                                              vd, it, s_ic, cx, k, acc);
-          if (z3)
-            accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
-          else
-            accumulate_plane<C, NP, UL, false>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+    if (!z3) {
+      // 2D: the item's steps are tiles down the image, one per stage, each
+      // with its own one-row halo.  A tile's centres are complete once its
+      // stage is read (8-neighbourhood in the plane); each is finalised during
+      // the next step, in the same basic block as that step's stencil, with
+      // the branch-free form when the whole warp allows it (as in 3D).  Slot
+      // sm takes the step's sums, sd holds the previous step's centre, whose
+      // column is cp.
+      bool ok = wait_full(q0);
+      Ctx cp = cx;
+      for (int kk = 0; kk < np; ++kk) {
+        const int qq = q0 + kk;
+        const bool has_next = kk + 1 < np;
+        const bool landed1 =
+            !has_next || mbar_test_wait(&full[(qq + 1) % NSTAGE],
+                                        static_cast<uint32_t>(((qq + 1) / NSTAGE) & 1));
+        const Ctx cc = column_ctx(it.x0 + tx, (it.pzb + kk) * TY + ty, vd);
+        const bool fin = kk >= 1 && cp.col_ok;
+        const bool all_g = __all_sync(0xffffffffu, !cp.col_ok || sd.G >= 1.0e-30f);
+        const bool all_live = __all_sync(0xffffffffu, cp.col_ok);
+        const bool any_live = __any_sync(0xffffffffu, cp.col_ok);
+        const bool fast = kk >= 1 && all_g && k.m_is_2 && any_live;
+        if (ok) {
+          const float* xs = xs_of(qq % NSTAGE);
+          const float* us = us_of(qq % NSTAGE);
+          const float x_mid = xs[cidx];
+          const int sdi = (qq + NSTAGE - 1) % NSTAGE;
+          if (fast && all_live) {
+            finalize_centre<C, NP, UL, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], 0, true, vd,
+                                             it, s_ic, cp, k, acc);
+            accumulate_plane<C, NP, UL, false>(xs, us, cidx, 0.0f, x_mid, 0.0f, sl, sm, sh);
+          } else if (fast) {
+            finalize_centre<C, NP, UL, true, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], 0,
+                                                   true, vd, it, s_ic, cp, k, acc, cp.col_ok);
+            accumulate_plane<C, NP, UL, false>(xs, us, cidx, 0.0f, x_mid, 0.0f, sl, sm, sh);
+          } else {
+            if (fin)
+              finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], 0,
+                                                cp.col_interior, vd, it, s_ic, cp, k, acc);
+            accumulate_plane<C, NP, UL, false>(xs, us, cidx, 0.0f, x_mid, 0.0f, sl, sm, sh);
+          }
         }
+        if (!landed1) ok = ok && wait_full(qq + 1);
+        if (kk >= 1) release(qq - 1);
+        sd = sm;
+        sm.clear();
+        cp = cc;
       }
-      if (!landed2) ok = ok && wait_full(qq + 2);
-      if (kk >= 2) release(qq - 2);
-    };
-    for (int kk = 0; kk < np; ++kk) {
-      step(kk, sd, sl, sm, sh);
-      sd = sl;
-      sl = sm;
-      sm = sh;
-      sh.clear();
-    }
-    // After the last plane: sd = centre pze - 1 (complete) and sl = centre pze
-    // (complete only when pze is the last plane of the volume).
-    {
       const int ql = q0 + np - 1;
-      const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
-      if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
-        const int sdi = (ql + NSTAGE - 1) % NSTAGE;
-        finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
-                               cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
-                               it, s_ic, cx, k, acc);
-      }
-      if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
-        const int sli = ql % NSTAGE;
-        finalize_centre<C, NP, UL, false>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
-                               cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
-      }
-      if (np >= 2) release(ql - 1);
+      if (cp.col_ok && !*reinterpret_cast<volatile int*>(&s_abort))
+        finalize_centre<C, NP, UL, false>(sd, us_of(ql % NSTAGE), cidx, xs_of(ql % NSTAGE)[cidx],
+                                          0, cp.col_interior, vd, it, s_ic, cp, k, acc);
       release(ql);
+    } else {
+      // sd / sl / sm / sh = centres pz - 2 (complete), pz - 1, pz, pz + 1 while
+      // plane pz is consumed.  The centre completed by plane pz - 1 is finalised
+      // in the same basic block as plane pz's stencil so that its dependency
+      // chain (Eqs 4 and 2) overlaps the stencil arithmetic.  Each stage is
+      // waited for once and one plane early: plane pz consumes stages pz - 2 ..
+      // pz + 1 (pz + 1 supplies x of the centre above), and the full barrier of
+      // stage pz + 2 is tested without blocking when plane pz starts, its result
+      // read only after plane pz's arithmetic; only a stage that had not landed
+      // by then is waited for (bounded).
+      bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
+      // One plane: finalise centre pz - 2 (slot sd), add plane pz to the centres
+      // pz - 1, pz and pz + 1 (slots sl, sm and sh; sh starts cleared).
+      auto step = [&](int kk, Slot<C, NP>& sd, Slot<C, NP>& sl, Slot<C, NP>& sm,
+                      Slot<C, NP>& sh) {
+        const int qq = q0 + kk;
+        const int pz = it.pzb + kk;
+        const bool has_next = kk + 1 < np;
+        const bool need2 = kk + 2 < np;
+        const bool landed2 =
+            !need2 || mbar_test_wait(&full[(qq + 2) % NSTAGE],
+                                     static_cast<uint32_t>(((qq + 2) / NSTAGE) & 1));
+        // centre pz - 2 is finalised here when it lies in the item's z-range;
+        // the whole warp takes the fast form when every lane can (voted by all
+        // 32 lanes, before any lane may skip the plane)
+        const int zd = pz - 2;
+        const bool fin_z = kk >= 2 && zd >= it.z0 && zd < it.z1;
+        const bool fin = fin_z && cx.col_ok;
+        const bool zin = zd > 0 && zd < vd.nz - 1;
+        const bool inter = cx.col_interior && zin;
+        const bool all_g = __all_sync(0xffffffffu, !cx.col_ok || sd.G >= 1.0e-30f);
+        const bool fast = fin_z && zin && all_g && k.m_is_2 && warp_any_live;
+        if (ok) {
+          const float* xs = xs_of(qq % NSTAGE);
+          const float* us = us_of(qq % NSTAGE);
+          const float x_mid = xs[cidx];
+          const float x_lo = kk > 0 ? xs_of((qq + NSTAGE - 1) % NSTAGE)[cidx] : 0.0f;
+          const float x_hi = has_next ? xs_of((qq + 1) % NSTAGE)[cidx] : 0.0f;
+          const int sdi = (qq + NSTAGE - 2) % NSTAGE;
+          if (fast && warp_all_live) {
+            finalize_centre<C, NP, UL, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, true, vd,
+                                             it, s_ic, cx, k, acc);
+            accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          } else if (fast) {      // a tile overhanging the volume: some lanes outside
+            finalize_centre<C, NP, UL, true, true>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd,
+                                                   true, vd, it, s_ic, cx, k, acc, cx.col_ok);
+            accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          } else {
+            if (fin)
+              finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], zd, inter,
+                                                vd, it, s_ic, cx, k, acc);
+            accumulate_plane<C, NP, UL, true>(xs, us, cidx, x_lo, x_mid, x_hi, sl, sm, sh);
+          }
+        }
+        if (!landed2) ok = ok && wait_full(qq + 2);
+        if (kk >= 2) release(qq - 2);
+      };
+      for (int kk = 0; kk < np; ++kk) {
+        step(kk, sd, sl, sm, sh);
+        sd = sl;
+        sl = sm;
+        sm = sh;
+        sh.clear();
+      }
+      // After the last plane: sd = centre pze - 1 (complete) and sl = centre pze
+      // (complete only when pze is the last plane of the volume).
+      {
+        const int ql = q0 + np - 1;
+        const bool live = cx.col_ok && !*reinterpret_cast<volatile int*>(&s_abort);
+        if (live && np >= 2 && it.pze - 1 >= it.z0 && it.pze - 1 < it.z1) {
+          const int sdi = (ql + NSTAGE - 1) % NSTAGE;
+          finalize_centre<C, NP, UL, false>(sd, us_of(sdi), cidx, xs_of(sdi)[cidx], it.pze - 1,
+                                 cx.col_interior && it.pze - 1 > 0 && it.pze - 1 < vd.nz - 1, vd,
+                                 it, s_ic, cx, k, acc);
+        }
+        if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
+          const int sli = ql % NSTAGE;
+          finalize_centre<C, NP, UL, false>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
+                                 cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
+        }
+        if (np >= 2) release(ql - 1);
+        release(ql);
+      }
     }
     q = q0 + np;
 
