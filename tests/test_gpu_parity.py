@@ -479,6 +479,30 @@ def test_every_plan_matches_oracle(G, c, np_, chunks):
     assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
 
 
+@pytest.mark.parametrize("chunks", [0, 1, 3, 10])
+def test_2d_runs_of_tiles_match_oracle(G, chunks):
+    # a 2D image of 100 rows (10 tiles of 11 rows, the last with one row: lanes
+    # outside the image in the masked form) and 45 columns (a ragged x tile);
+    # chunks cut each column of tiles into runs: the rule (0), whole columns
+    # (1), runs of 4, 4 and 2 tiles (3), one tile per item (10)
+    shape = (1, 100, 45)
+    x = unit_volume(shape, seed=141)
+    U0 = phantoms.random_memberships(shape, 4, seed=142)
+    C0 = np.sort(np.random.default_rng(143).random(4))
+    lam_xi = np.random.default_rng(144).random((6, 2)) * 0.6
+    if chunks:
+        G.force_plan(2, chunks)
+    try:
+        fit, its, _ = G.pso_fitness_batch(dev_vol(x), G.Params(c=4, max_iter=6, eps_u=0.0),
+                                          lam_xi, dev_u(U0), C0, nx=shape[2])
+    finally:
+        G.force_plan(0)
+    fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
+                              max_iter=6, eps=0.0)
+    assert np.array_equal(its.cpu().numpy(), io)
+    assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
+
+
 def test_autotuned_plan_is_cached_and_matches_oracle(G):
     shape = (24, 40, 70)
     x = unit_volume(shape, seed=131)
