@@ -207,7 +207,7 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
 /* ---------------------------------------------------------------------------
  * Work decomposition of the batched stencil launches (no arithmetic change
  * beyond the order of the FP64 partial sums).  A launch is cut into work
- * items of np particles (1, or 2 for c <= 4) x a 32-column tile x a z-chunk
+ * items of np particles (1, or 2 for c <= 5) x a 32-column tile x a z-chunk
  * of tz planes (in a 2D image: a run of tz tiles down the image, the tiles
  * taking the place of the planes).  Mode 0 (default): a built-in rule picks
  * the deepest chunks that still give every CTA four items.  Mode 1: the first
@@ -220,7 +220,7 @@ ifcm_status pso_fitness_batch(const float* x, ifcm_shape shape, const ifcm_param
 void ifcm_autotune_enable(int32_t mode);
 void ifcm_autotune_reset(void);
 /* Every later launch uses np particles per item (where c allows it: np = 2
- * only for c <= 4, else the usual choice) and `chunks` z-chunks per tile
+ * only for c <= 5, else the usual choice) and `chunks` z-chunks per tile
  * (clamped so that chunks keep >= 8 planes).  np = 0 lifts it.  For tests
  * and experiments.  IFCM_ERR_INVALID for np outside 0..2 or chunks < 1. */
 ifcm_status ifcm_stencil_force_plan(int32_t np, int32_t chunks);

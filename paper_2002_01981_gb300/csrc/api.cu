@@ -193,7 +193,7 @@ struct RunBufs {
 size_t run_buffer_elems(int c, int P, int layout) {
   if (layout == UL_PLANAR) return static_cast<size_t>(P) * c;
   long long w = pair_unit_words(c, 1, P);
-  if (c <= 4 && pair_unit_words(c, 2, P) > w) w = pair_unit_words(c, 2, P);
+  if (c <= 5 && pair_unit_words(c, 2, P) > w) w = pair_unit_words(c, 2, P);
   if (layout == UL_F32P) w *= 2;          // 8-byte words
   // the FCM start (FP32 planes, one particle) also runs in these buffers
   if (w < c) w = c;

@@ -20,10 +20,10 @@ PIFCM_STENCIL_FAMILY(f32p_np2)
 
 bool stencil_np_supported(int c, int np) {
   if (c < 2 || c > kMaxC) return false;
-  return np == 1 || (np == 2 && c <= 4);
+  return np == 1 || (np == 2 && c <= 5);
 }
 
-int stencil_default_np(int c) { return c <= 4 ? 2 : 1; }
+int stencil_default_np(int c) { return c <= 5 ? 2 : 1; }
 
 long long pair_unit_words(int c, int np, int P) {
   return np == 2 ? static_cast<long long>((P + 1) / 2) * c

@@ -1,5 +1,5 @@
 // The stencil kernel over bf16 pair words with two particles per work item
-// (c <= 4): word (pair k, cluster j) holds cluster j of particles 2k and
+// (c <= 5): word (pair k, cluster j) holds cluster j of particles 2k and
 // 2k+1, the two lanes of the packed FP32x2 sums.
 #include "stencil_kernel.cuh"
 
@@ -9,7 +9,8 @@ size_t smem_bytes_bf16_np2(int c) {
   switch (c) {
     case 2: return smem_total<2, 2, UL_BF16>();
     case 3: return smem_total<3, 2, UL_BF16>();
-    default: return smem_total<4, 2, UL_BF16>();
+    case 4: return smem_total<4, 2, UL_BF16>();
+    default: return smem_total<5, 2, UL_BF16>();
   }
 }
 
@@ -17,7 +18,8 @@ int blocks_per_sm_bf16_np2(int c) {
   switch (c) {
     case 2: return blocks_per_sm_c<2, 2, UL_BF16>();
     case 3: return blocks_per_sm_c<3, 2, UL_BF16>();
-    default: return blocks_per_sm_c<4, 2, UL_BF16>();
+    case 4: return blocks_per_sm_c<4, 2, UL_BF16>();
+    default: return blocks_per_sm_c<5, 2, UL_BF16>();
   }
 }
 
@@ -26,6 +28,7 @@ cudaError_t launch_stencil_bf16_np2(int c, const StencilArgs& a, int grid, cudaS
     case 2: return launch_c<2, 2, UL_BF16>(a, grid, s);
     case 3: return launch_c<3, 2, UL_BF16>(a, grid, s);
     case 4: return launch_c<4, 2, UL_BF16>(a, grid, s);
+    case 5: return launch_c<5, 2, UL_BF16>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,5 +1,5 @@
 // The stencil kernel over float2 pair words with two particles per work item
-// (c <= 4): word (pair k, cluster j) holds cluster j of particles 2k and 2k+1,
+// (c <= 5): word (pair k, cluster j) holds cluster j of particles 2k and 2k+1,
 // loaded and stored as one 64-bit access.  The FP32 layout of batched runs.
 #include "stencil_kernel.cuh"
 
@@ -9,7 +9,8 @@ size_t smem_bytes_f32p_np2(int c) {
   switch (c) {
     case 2: return smem_total<2, 2, UL_F32P>();
     case 3: return smem_total<3, 2, UL_F32P>();
-    default: return smem_total<4, 2, UL_F32P>();
+    case 4: return smem_total<4, 2, UL_F32P>();
+    default: return smem_total<5, 2, UL_F32P>();
   }
 }
 
@@ -17,7 +18,8 @@ int blocks_per_sm_f32p_np2(int c) {
   switch (c) {
     case 2: return blocks_per_sm_c<2, 2, UL_F32P>();
     case 3: return blocks_per_sm_c<3, 2, UL_F32P>();
-    default: return blocks_per_sm_c<4, 2, UL_F32P>();
+    case 4: return blocks_per_sm_c<4, 2, UL_F32P>();
+    default: return blocks_per_sm_c<5, 2, UL_F32P>();
   }
 }
 
@@ -26,6 +28,7 @@ cudaError_t launch_stencil_f32p_np2(int c, const StencilArgs& a, int grid, cudaS
     case 2: return launch_c<2, 2, UL_F32P>(a, grid, s);
     case 3: return launch_c<3, 2, UL_F32P>(a, grid, s);
     case 4: return launch_c<4, 2, UL_F32P>(a, grid, s);
+    case 5: return launch_c<5, 2, UL_F32P>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

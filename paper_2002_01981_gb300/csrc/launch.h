@@ -61,7 +61,7 @@ static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay be
 // FP32 planes per particle, bf16 pair words, or float2 pair words.
 constexpr int UL_PLANAR = 0, UL_BF16 = 1, UL_F32P = 2;
 
-// np = particles sharing one work item: 1 for every c, 2 for c <= 4.
+// np = particles sharing one work item: 1 for every c, 2 for c <= 5.
 bool stencil_np_supported(int c, int np);
 int stencil_default_np(int c);
 size_t stencil_smem_bytes(int c, int np, int layout);

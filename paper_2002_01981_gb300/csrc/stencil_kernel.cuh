@@ -627,7 +627,10 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
   }
 }
 
-template <int C, int NP, int UL>
+// FLAT selects the volumes a launch of this instantiation works on: the 2D
+// images (FLAT) or the 3D volumes; the other kind gets no items.  The two
+// plane loops are compiled apart so that neither shapes the other's code.
+template <int C, int NP, int UL, bool FLAT>
 __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     stencil_kernel(const __grid_constant__ StencilArgs a) {
   extern __shared__ unsigned char dsmem_raw[];
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   constexpr bool kPairUnits = paired(UL) && NP == 2;
   for (int v = warp; v < a.n_vol; v += NT / 32) {
     const VolDesc& vd = a.vol[v];
-    const int units = kPairUnits ? (vd.P + 1) / 2 : vd.P;
+    const int units = (vd.nz == 1) != FLAT ? 0 : kPairUnits ? (vd.P + 1) / 2 : vd.P;
     int n = 0;
     for (int base = 0; base < units; base += 32) {
       const int p = base + lane;
@@ -714,8 +717,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
           }
           if (*reinterpret_cast<volatile int*>(&s_abort)) return;
           // a plane of the tile's column, or in 2D the tile of step pz
-          const int ty0 = vd.nz == 1 ? pz * TY : it.y0;
-          const int tz0 = vd.nz == 1 ? 0 : pz;
+          const int ty0 = FLAT ? pz * TY : it.y0;
+          const int tz0 = FLAT ? 0 : pz;
           mbar_arrive_expect_tx(&full[s], stage_tx_bytes<C, NP, UL>());
           tma_load_3d(xs_of(s), mx, &full[s], it.x0 - 4, ty0 - 1, tz0);
           tma_load_4d(us_of(s), mu, &full[s], it.x0 - 4, ty0 - 1, tz0,
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const Item it = decode_item<NP, UL>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
-    const bool z3 = vd.nz > 1;
+    constexpr bool z3 = !FLAT;
     const int plane = vd.nz * vd.ny * vd.pitch;
     // the thread's column (in 2D: its column in the item's first tile)
     const Ctx cx = column_ctx(it.x0 + tx, it.y0 + ty, vd);
@@ -799,7 +802,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     const int np = it.pze - it.pzb + 1;
     const int q0 = q;
 
-    if (!z3) {
+    if (FLAT) {
       // 2D: the item's steps are tiles down the image, one per stage, each
       // with its own one-row halo.  A tile's centres are complete once its
       // stage is read (8-neighbourhood in the plane); each is finalised during
@@ -987,24 +990,41 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   }
 }
 // ---------------------------------------------------------------------------
+// One iteration over the launch's volumes: the 3D kernel if it has 3D
+// volumes, the 2D kernel if it has 2D images (both, one after the other on
+// the stream, for a batch that mixes them).
 template <int C, int NP, int UL>
 cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
   constexpr int smem = smem_total<C, NP, UL>();
-  cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  stencil_kernel<C, NP, UL><<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
+  bool flat = false, deep = false;
+  for (int v = 0; v < a.n_vol; ++v) (a.vol[v].nz == 1 ? flat : deep) = true;
+  if (deep) {
+    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    stencil_kernel<C, NP, UL, false><<<grid, NT, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (flat) {
+    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    stencil_kernel<C, NP, UL, true><<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
+// CTAs per SM (the 3D kernel; both have the same shared memory and block).
 template <int C, int NP, int UL>
 int blocks_per_sm_c() {
   int n = 0;
   constexpr int smem = smem_total<C, NP, UL>();
-  cudaFuncSetAttribute(stencil_kernel<C, NP, UL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP, UL>, NT, smem) !=
-      cudaSuccess)
+  cudaFuncSetAttribute(stencil_kernel<C, NP, UL, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<C, NP, UL, false>, NT,
+                                                    smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }

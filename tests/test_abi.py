@@ -210,11 +210,13 @@ def test_stencil_plan_rule_and_forcing(lib):
     shp = N.IfcmShape(181, 217, 181, 184)
     assert lib.ifcm_stencil_plan(shp, 4, 20, ctypes.byref(npp), ctypes.byref(tz)) == 0
     assert npp.value == 2 and 8 <= tz.value <= 181
+    assert lib.ifcm_stencil_plan(shp, 5, 20, ctypes.byref(npp), ctypes.byref(tz)) == 0
+    assert npp.value == 2
     assert lib.ifcm_stencil_plan(shp, 6, 20, ctypes.byref(npp), ctypes.byref(tz)) == 0
     assert npp.value == 1
     assert lib.ifcm_stencil_plan(shp, 9, 20, ctypes.byref(npp), ctypes.byref(tz)) == -1
     assert lib.ifcm_stencil_plan(N.IfcmShape(5, 4, 3, 6), 4, 20, None, None) == -1
-    # forcing: chunks are clamped to >= 8 planes; np = 2 is ignored above c = 4
+    # forcing: chunks are clamped to >= 8 planes; np = 2 is ignored above c = 5
     assert lib.ifcm_stencil_force_plan(3, 1) == 1
     assert lib.ifcm_stencil_force_plan(1, 0) == 1
     assert lib.ifcm_stencil_force_plan(1, 100) == 0
@@ -223,7 +225,7 @@ def test_stencil_plan_rule_and_forcing(lib):
     assert lib.ifcm_stencil_force_plan(2, 4) == 0
     lib.ifcm_stencil_plan(shp, 4, 20, ctypes.byref(npp), ctypes.byref(tz))
     assert (npp.value, tz.value) == (2, 46)
-    lib.ifcm_stencil_plan(shp, 5, 20, ctypes.byref(npp), ctypes.byref(tz))
+    lib.ifcm_stencil_plan(shp, 6, 20, ctypes.byref(npp), ctypes.byref(tz))
     assert npp.value == 1
     assert lib.ifcm_stencil_force_plan(0, 0) == 0
     # a 2D image: an item is a run of tiles down the image (64 rows = 6 tiles of

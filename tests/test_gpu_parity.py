@@ -458,7 +458,8 @@ def test_fitness_multi_beyond_one_launch(G):
 
 # ------------------------------------------------ work decomposition plans
 @pytest.mark.parametrize("c,np_,chunks", [(4, 1, 1), (4, 2, 1), (4, 1, 3), (4, 2, 100),
-                                          (3, 1, 2), (6, 1, 1), (6, 1, 100), (2, 2, 4)])
+                                          (3, 1, 2), (5, 2, 1), (5, 2, 3), (5, 1, 2),
+                                          (6, 1, 1), (6, 1, 100), (2, 2, 4)])
 def test_every_plan_matches_oracle(G, c, np_, chunks):
     # z = 37 planes: up to five chunks (the last one ragged), x and y tails too
     shape = (37, 30, 70)

@@ -129,7 +129,8 @@ def test_bf16_flat_neighbourhoods(G):
         assert abs(Jg - Jm) <= J_RTOL_MODEL * abs(Jm)
 
 
-@pytest.mark.parametrize("c,np_,eps", [(4, 2, 2e-3), (3, 2, 2e-3), (4, 1, 2e-3), (6, 1, 1e-2)])
+@pytest.mark.parametrize("c,np_,eps", [(4, 2, 2e-3), (3, 2, 2e-3), (4, 1, 2e-3), (5, 2, 1e-2),
+                                       (6, 1, 1e-2)])
 def test_bf16_batch_equals_single_runs(G, c, np_, eps):
     # odd P (the last pair has one particle) and eps > 0 (particles of a pair
     # stop at different iterations): each particle's fitness and iteration
