@@ -784,7 +784,7 @@ def run_ours(args):
                 "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic_pu * per_launch_updates if traffic_pu else None,
                 "algorithmic_bytes_per_launch": per_launch_updates * bytes_per_update,
-                "kernel": f"stencil_kernel<4,{plan_np},UL_F32P>",
+                "kernel": f"stencil_kernel<4,{plan_np},UL_F32P,3D>",
                 "plan": {"particles_per_item": plan_np, "tz": plan_tz,
                          "tile": "32x11 columns", "memberships": "float2 pair words"},
                 "kernel_ms_total": kernel_ms,
