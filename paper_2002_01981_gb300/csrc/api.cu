@@ -1403,7 +1403,8 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c.
   ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter, rb,
                    b.iters_init, b.c0, b.J_init, b.status, false, st));
-  CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0, static_cast<long long>(c) * rpl, st));
+  CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0,
+                            static_cast<long long>(c) * rpl, st));
 
   // Algorithm 1 steps 3-9.
   pso_state sw{};

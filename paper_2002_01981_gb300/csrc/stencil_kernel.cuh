@@ -4,20 +4,21 @@
 //
 // Work item = (group of NP particles, TX x TY column tile, z-chunk of tz
 // planes); in a 2D image (group, column of tiles, run of tz tiles down the
-// image), the tiles taking the place of the planes.  The last warp of each CTA (warp TY) is the producer: one lane
-// walks the CTA's items plane by plane and, for each plane, issues TMA tile
-// loads of the normalised volume x and of the c membership planes U^t of each
-// particle of the group (one-voxel halo in y, aligned four-voxel margins in x)
-// into a ring of shared-memory stages, gated by "full" (transaction bytes) and
-// "empty" (one arrival per consumer warp) mbarriers.  Warps 0 .. TY-1 are
-// consumers: thread (tx, ty) owns column (x0 + tx, y0 + ty) and keeps four
-// centres of the column in registers.  The plane being consumed contributes to the centre below it
-// (dz = +1), its own centre (dz = 0) and the centre above (dz = -1); the
-// centre two planes below, completed by the previous plane, is finalised in
-// the same step so that its long dependency chain overlaps the stencil
-// arithmetic.  The per-centre sums are float2 pairs (the two particles of an
-// item, or two clusters) updated with packed FP32x2 instructions.  A plane's
-// stage is released once the centre it holds has been finalised:
+// image), the tiles taking the place of the planes.  The last warp of each CTA
+// (warp TY) is the producer: one lane walks the CTA's items plane by plane
+// and, for each plane, issues TMA tile loads of the normalised volume x and of
+// the c membership planes U^t of each particle of the group (one-voxel halo in
+// y, aligned four-voxel margins in x) into a ring of shared-memory stages,
+// gated by "full" (transaction bytes) and "empty" (one arrival per consumer
+// warp) mbarriers.  Warps 0 .. TY-1 are consumers: thread (tx, ty) owns column
+// (x0 + tx, y0 + ty) and keeps four centres of the column in registers.  The
+// plane being consumed contributes to the centre below it (dz = +1), its own
+// centre (dz = 0) and the centre above (dz = -1); the centre two planes below,
+// completed by the previous plane, is finalised in the same step so that its
+// long dependency chain overlaps the stencil arithmetic.  The per-centre sums
+// are float2 pairs (the two particles of an item, or two clusters) updated
+// with packed FP32x2 instructions.  A plane's stage is released once the
+// centre it holds has been finalised:
 // H = sum u g / sum g, F = sum u^2 q^2 / sum q^2 (q^2 = dx^2+dy^2+dz^2,
 // reading R1), Eqs 4 and 2, U^{t+1} written from registers, and the centre's
 // shares of sum u^m, sum u^m x, J and max|du|.
@@ -77,7 +78,7 @@ constexpr int TX = kTX, TY = kTY;
 constexpr int NCW = TY;                // consumer warps, one per row of the tile
 constexpr int NCT = NCW * 32;          // consumer threads (one per column of the tile)
 constexpr int NT = NCT + 32;           // + one producer warp
-constexpr int BX = TX + 8;             // x box: 4-voxel aligned margins (TMA x must be 16-B aligned)
+constexpr int BX = TX + 8;             // x box: 4-voxel margins (TMA x must be 16-B aligned)
 constexpr int BY = TY + 2;             // y box: one-voxel halo
 constexpr int PLANE = BX * BY;         // floats in one channel of a stage
 #ifndef PIFCM_STENCIL_STAGES
@@ -210,7 +211,7 @@ __device__ __forceinline__ Item decode_item(const StencilArgs& a, const ItemTabl
   it.x0 = tx * TX;
   it.y0 = ty * TY;
   it.z0 = zc * vd.tz;
-  if (vd.nz == 1) {   // 2D: steps z0 .. z1 - 1 are tiles down the image (rows 11 z ..)
+  if (vd.nz == 1) {   // 2D: steps z0 .. z1 - 1 are tiles down the image, tile z at rows TY z ..
     it.z1 = min(it.z0 + vd.tz, (vd.ny + TY - 1) / TY);
     it.pzb = it.z0;
     it.pze = it.z1 - 1;
@@ -761,7 +762,6 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const Item it = decode_item<NP, UL>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
-    constexpr bool z3 = !FLAT;
     const int plane = vd.nz * vd.ny * vd.pitch;
     // the thread's column (in 2D: its column in the item's first tile)
     const Ctx cx = column_ctx(it.x0 + tx, it.y0 + ty, vd);
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1) {
           const int sli = ql % NSTAGE;
           finalize_centre<C, NP, UL, false>(sl, us_of(sli), cidx, xs_of(sli)[cidx], it.pze,
-                                 cx.col_interior && !z3, vd, it, s_ic, cx, k, acc);
+                                 false, vd, it, s_ic, cx, k, acc);   // the top z face
         }
         if (np >= 2) release(ql - 1);
         release(ql);
