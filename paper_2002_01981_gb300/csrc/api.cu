@@ -181,6 +181,7 @@ struct RunBufs {
   float* ua[kMaxVols];
   float* ub[kMaxVols];
   float* u0p[kMaxVols];
+  float* gs[kMaxVols];          // 1/G per voxel (gsum_kernel), one plane per volume
   int pbase[kMaxVols];
   long long rec_base[kMaxVols];
   int rec_per_particle[kMaxVols];
@@ -213,6 +214,7 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
     r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
     r.u0p[v] = layout == UL_PLANAR ? nullptr
                : cv.take<float>(static_cast<size_t>(c) * pl * (layout == UL_F32P ? 2 : 1));
+    r.gs[v] = cv.take<float>(pl);
     const long long nvox = static_cast<long long>(shapes[v].nx) * shapes[v].ny * shapes[v].nz;
     int nrec = max_tiles(shapes[v]);
     const int nplain = plain_blocks(nvox, kPlainVpt);      // the plain kernel's records (P = 1)
@@ -316,6 +318,24 @@ ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (memberships) failed: %d", (int)r);
+  return IFCM_OK;
+}
+
+// The 1/G planes of a volume (gsum_kernel's output): one 32 x TY box of the
+// tile's centres per plane; positions outside the volume read as 0.
+ifcm_status make_smap(CUtensorMap* m, const float* base, const ifcm_shape& s) {
+  ST_TRY(get_encode());
+  const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * 4;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
+                        static_cast<cuuint64_t>(s.nz)};
+  cuuint64_t strides[2] = {row, row * s.ny};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(kTX), static_cast<cuuint32_t>(kTY), 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (1/G) failed: %d", (int)r);
   return IFCM_OK;
 }
 
@@ -463,6 +483,7 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
   a.partials = rb.partials;
   a.dmax = rb.dmax;
   a.status = status;
+  a.sum_one = kind != 0;   // later iterations read Eq 2's memberships
   fill_method(a, p);
   for (int v = 0; v < n; ++v) {
     const BatchVol& bv = vols[v];
@@ -484,6 +505,7 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.lam_xi = bv.lam_xi;
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
     ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
+    ST_TRY(make_smap(&a.tm_s[v], rb.gs[v], s));
     if (rb.layout != UL_PLANAR) {
       // pair words: K planes per unit (a particle pair for np = 2, a particle
       // for np = 1); iteration 0 reads the packed shared start (one unit)
@@ -638,6 +660,13 @@ struct BatchRun {
       P_total += vols[v].P;
     }
     if (!wide) {
+      // 1/G of each 3D volume for the float2-pair kernel (plans are timed on it)
+      if (rb->layout == UL_F32P)
+        for (int v = 0; v < n; ++v) {
+          const ifcm_shape& s = vols[v].shape;
+          if (s.nz > 1)
+            CU_TRY(launch_gsum(vols[v].x, s.nx, s.ny, s.nz, s.pitch_x, rb->gs[v], st));
+        }
       ST_TRY(choose_plan(vols, n, p, *rb, status, st, &pl));
       rb->np = pl.np;
       ST_TRY(pack_starts(vols, n, c, *rb, pl.np, st));

@@ -153,6 +153,39 @@ __global__ void unpack_select_kernel(const W* a, const W* b, const int32_t* iter
   }
 }
 
+// 1/G of every voxel of a 3D volume (G = sum over the in-volume neighbours of
+// |x_i - x_k|, Eqs 5-6; reading R4), summed in FP64 and rounded once; a flat
+// neighbourhood (G = 0, reading R3) is stored as -1/n (n in-volume
+// neighbours), and a G below FP32's range as the largest float.
+__global__ void gsum_kernel(const float* __restrict__ x, int nx, int ny, int nz, int pitch,
+                            float* __restrict__ out) {
+  const long long n = static_cast<long long>(nx) * ny * nz;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int X = static_cast<int>(i % nx);
+    const long long r = i / nx;
+    const int Y = static_cast<int>(r % ny), Z = static_cast<int>(r / ny);
+    const float xi = x[(static_cast<long long>(Z) * ny + Y) * pitch + X];
+    double G = 0.0;
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+          if ((dx == 0 && dy == 0 && dz == 0) || kx < 0 || kx >= nx || ky < 0 || ky >= ny ||
+              kz < 0 || kz >= nz)
+            continue;
+          G += fabs(static_cast<double>(xi) -
+                    static_cast<double>(x[(static_cast<long long>(kz) * ny + ky) * pitch + kx]));
+          ++cnt;
+        }
+    float s;
+    if (G > 0.0) s = static_cast<float>(fmin(1.0 / G, 3.4028234663852886e38));
+    else s = cnt > 0 ? -1.0f / static_cast<float>(cnt) : 0.0f;
+    out[(static_cast<long long>(Z) * ny + Y) * pitch + X] = s;
+  }
+}
+
 __global__ void fill_kernel(float* dst, float value, long long n) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -349,6 +382,16 @@ cudaError_t launch_fill(float* dst, float value, long long n, cudaStream_t s) {
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   fill_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(dst, value, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsum(const float* x, int nx, int ny, int nz, int pitch, float* s_out,
+                        cudaStream_t s) {
+  const long long n = static_cast<long long>(nx) * ny * nz;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  gsum_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(x, nx, ny, nz, pitch, s_out);
   return cudaGetLastError();
 }
 

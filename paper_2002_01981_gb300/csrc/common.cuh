@@ -74,15 +74,27 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on one phase of an mbarrier.  Each try_wait suspends the
-// thread for a hardware-chosen interval; after `limit` unsuccessful tries the
-// wait gives up and returns false so that the caller can record
-// IFCM_ERR_TIMEOUT and leave instead of spinning forever.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Default bound of a wait: about one second.
+constexpr uint64_t kWaitLimitNs = 1ull << 30;
+
+// Bounded wait on one phase of an mbarrier.  After limit_ns nanoseconds of
+// %globaltimer without the phase completing, the wait gives up and returns
+// false, so that the caller can record IFCM_ERR_TIMEOUT and leave instead of
+// spinning forever.  A limit of 0 gives up at the first unsuccessful try.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  uint32_t limit = (1u << 22)) {
-  for (uint32_t i = 0; i < limit; ++i)
+                                                  uint64_t limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 >= limit_ns) return false;
+  }
 }
 
 // 3D / 4D tiled TMA loads into shared memory, completing on `bar`.

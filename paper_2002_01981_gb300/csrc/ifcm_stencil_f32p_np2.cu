@@ -1,9 +1,23 @@
 // The stencil kernel over float2 pair words with two particles per work item
 // (c <= 5): word (pair k, cluster j) holds cluster j of particles 2k and 2k+1,
 // loaded and stored as one 64-bit access.  The FP32 layout of batched runs.
-#include "stencil_kernel.cuh"
+// Iterations that read Eq 2's memberships (every one after the first) with
+// m = 2 run the 3D volumes through stencil3d_kernel.
+#include "stencil3d.cuh"
 
 namespace pifcm {
+
+namespace {
+template <int C>
+cudaError_t launch_np2(const StencilArgs& a, int grid, cudaStream_t s) {
+  bool deep = false;
+  for (int v = 0; v < a.n_vol; ++v) deep = deep || a.vol[v].nz > 1;
+  if (!deep || !a.sum_one || !a.m_is_2) return launch_c<C, 2, UL_F32P>(a, grid, s);
+  cudaError_t e = launch3d_c<C>(a, grid, s);
+  if (e != cudaSuccess) return e;
+  return launch_c<C, 2, UL_F32P>(a, grid, s, false);    // the 2D images of the batch
+}
+}  // namespace
 
 size_t smem_bytes_f32p_np2(int c) {
   switch (c) {
@@ -25,10 +39,10 @@ int blocks_per_sm_f32p_np2(int c) {
 
 cudaError_t launch_stencil_f32p_np2(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, 2, UL_F32P>(a, grid, s);
-    case 3: return launch_c<3, 2, UL_F32P>(a, grid, s);
-    case 4: return launch_c<4, 2, UL_F32P>(a, grid, s);
-    case 5: return launch_c<5, 2, UL_F32P>(a, grid, s);
+    case 2: return launch_np2<2>(a, grid, s);
+    case 3: return launch_np2<3>(a, grid, s);
+    case 4: return launch_np2<4>(a, grid, s);
+    case 5: return launch_np2<5>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,6 +44,7 @@ struct VolDesc {
 struct StencilArgs {
   CUtensorMap tm_x[kMaxVols];   // normalised volume (NaN outside)
   CUtensorMap tm_u[kMaxVols];   // memberships U^t (zero outside)
+  CUtensorMap tm_s[kMaxVols];   // 1/G per voxel (gsum_kernel), 32 x TY boxes (3D kernel)
   VolDesc vol[kMaxVols];
   int n_vol;
   const double* centres;        // [particles of the launch][c]  C^t
@@ -53,6 +54,7 @@ struct StencilArgs {
   float dist_floor, m, inv_m1;
   int m_is_2;
   int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across warps
+  int sum_one;                  // U^t comes from Eq 2 (memberships of a voxel sum to one)
   DevStatus* status;
 };
 static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
@@ -182,6 +184,11 @@ cudaError_t launch_scale(const float* v, float* x, int nx, int ny, int nz, int p
                          const float* pmin, const float* pmax, const int32_t* pbad, int nparts,
                          DevStatus* st, cudaStream_t s);
 cudaError_t launch_fill(float* dst, float value, long long n, cudaStream_t s);
+// s_i = 1/G_i with G_i = sum of |x_i - x_k| over the in-volume 26-neighbourhood
+// (FP64), or -1/n_i where G_i = 0 (n_i in-volume neighbours, 0 for none), for
+// every voxel of a 3D volume [nz][ny][pitch] (padding columns untouched).
+cudaError_t launch_gsum(const float* x, int nx, int ny, int nz, int pitch, float* s_out,
+                        cudaStream_t s);
 cudaError_t launch_select_copy(const float* a, const float* b, const int32_t* iters,
                                float* dst, long long n, cudaStream_t s);
 // Pair words of a shared start: u0 [c][plane] FP32 -> [c][plane] words (u, u)

@@ -1,0 +1,514 @@
+// Batched IFCM iteration over 3D volumes, two particles per work item, FP32
+// memberships in float2 pair words, m = 2: the neighbourhood stencil of Eqs
+// 5-9 fused with Eq 4 (distance), Eq 2 (membership), Eq 1 (objective) and the
+// centre sums of Eq 3.  This is the form of the batched fitness evaluation
+// (Algorithm 1 step 4) that carries almost all of a run's time; every other
+// case (2D images, m != 2, one particle, bf16 words, the first iteration from
+// a caller's start) runs stencil_kernel (stencil_kernel.cuh).
+//
+// Work decomposition, ring and producer are those of stencil_kernel: items of
+// (pair of particles, 32 x TY column tile, z-chunk), a TMA producer warp
+// feeding an 8-stage ring of planes, one consumer thread per column marching
+// up z.  What differs is the consumer's plane step, written for the fewest
+// instructions per update:
+//
+// - G_i = sum_k g_ik does not change between iterations (x is fixed), so it is
+//   computed once per volume (gsum_kernel, in FP64) and stored as s_i = 1/G_i.
+//   A flat neighbourhood (G_i = 0, reading R3) is stored as s_i = -1/n_i with
+//   n_i its in-volume neighbours: the stencil then takes g_ik = max(|x_i -
+//   x_k|, e_i) with e_i = 1 for such a voxel and 0 otherwise, which gives
+//   every in-volume neighbour weight 1 and turns H into the plain mean, with
+//   no branch.  (Out-of-volume neighbours hold u = 0, so their weight never
+//   counts, and |s_i| = 1/n_i divides by the in-volume count.)
+// - Memberships of one voxel sum to one (Eq 2), so sum_j H_ij = 1 and the last
+//   cluster's H is 1 - sum_{j<c-1} H_ij: its 26 neighbour products are not
+//   formed.  U^t always comes from Eq 2 here (iteration 0, which reads the
+//   caller's start, runs stencil_kernel).
+// - F needs no per-centre accumulation across planes beyond one float2 per
+//   cluster: each plane's window sums W0 (centre), S1 (faces), S2 (corners) of
+//   u^2 give A = W0 + 2 S1 + 3 S2 (weight 1 + dx^2 + dy^2, to the centres
+//   above and below) and V = S1 + 2 S2 (weight dx^2 + dy^2, to the centre in
+//   the plane).
+// - No warp votes or branches in the plane step: out-of-volume lanes of an
+//   overhanging tile compute on (x reads NaN there) but their stores are
+//   predicated off and their sums are zeroed once per item; the z-face
+//   centres differ only in 1/Q, a step argument.
+// - The four centre slots change roles, not values: the steady-state loop is
+//   unrolled four planes deep (slot roles rotate statically), with a short
+//   generic step (slot values rotated) for the first and last planes of an
+//   item.
+// - Shared-memory reads are plain LDS with immediate offsets from one base
+//   per stage (the stage pointers keep the shared address space).
+#pragma once
+
+#include "stencil_kernel.cuh"
+
+namespace pifcm {
+
+namespace {
+
+constexpr int SBYTES = ((TX * TY * 4 + 127) / 128) * 128;   // 1/G of the tile's centres
+
+template <int C>
+__host__ __device__ constexpr int s3_stage_bytes() {
+  return XBYTES + SBYTES + ublock_bytes<C, 2, UL_F32P>();
+}
+template <int C>
+__host__ __device__ constexpr uint32_t s3_tx_bytes() {
+  return static_cast<uint32_t>(PLANE * 4 + TX * TY * 4 + C * PLANE * 8);
+}
+template <int C>
+__host__ __device__ constexpr int s3_smem_total() {
+  return NSTAGE * s3_stage_bytes<C>() + 128;
+}
+static_assert(NSTAGE == 8, "stage indices are taken modulo 8 with a mask");
+static_assert(SBYTES % 128 == 0, "TMA destinations start on 128-byte boundaries");
+
+// One centre of the column: its sums over the planes read so far.
+template <int C>
+struct Slot3 {
+  static constexpr int KH = C - 1;   // clusters whose H is summed (the last by complement)
+  float2 H[KH];                      // sum_k u_kj g_ik, pair = the item's two particles
+  float2 F[C];                       // sum_k u_kj^2 q^2_ik
+  float x;                           // x_i
+  float s;                           // 1/G_i, or -1/n_i for a flat neighbourhood
+  float e;                           // floor of g_ik: 1 for a flat neighbourhood, else 0
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int q = 0; q < KH; ++q) H[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < C; ++q) F[q] = make_float2(0.0f, 0.0f);
+    x = s = e = 0.0f;
+  }
+};
+
+// Constants of an item, paired like the sums.
+template <int C>
+struct Fin3 {
+  float2 ncc[C];                     // -c_j of the two particles
+  float2 nlam, nxi;                  // -lambda, -xi of the two particles
+  float floor;                       // dist_floor
+};
+
+template <int C>
+struct Acc3 {
+  float2 s0[C], s1[C];               // sum u^m, sum u^m x
+  float2 J, dm;                      // J, max|du| of the two particles
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int q = 0; q < C; ++q) s0[q] = s1[q] = make_float2(0.0f, 0.0f);
+    J = dm = make_float2(0.0f, 0.0f);
+  }
+};
+
+// Finalise centre d: Eqs 5 and 7 (1/G from s, the last cluster's H by
+// complement), Eq 4 with reading R2, Eq 2 for m = 2, the U^{t+1} store and
+// the centre's shares of Eqs 1 and 3 and of max|du|.  ud: the centre's U^t
+// in its stage (pair words at its column); dst: its U^{t+1} word of pair 0.
+template <int C>
+__device__ __forceinline__ void fin3(const Slot3<C>& d, const float2* __restrict__ ud, float invq,
+                                     const Fin3<C>& fc, Acc3<C>& acc, float2* __restrict__ dst,
+                                     int plane, bool st) {
+  constexpr int KH = C - 1;
+  const float ig = fabsf(d.s);
+  float2 H[C], F[C];
+  float2 hs = d.H[0];
+#pragma unroll
+  for (int q = 1; q < KH; ++q) hs = __fadd2_rn(hs, d.H[q]);
+#pragma unroll
+  for (int q = 0; q < KH; ++q) H[q] = __fmul2_rn(d.H[q], dup2(ig));
+  H[C - 1] = __ffma2_rn(hs, dup2(-ig), dup2(1.0f));          // 1 - sum_{j<c-1} H_j
+#pragma unroll
+  for (int q = 0; q < C; ++q) F[q] = __fmul2_rn(d.F[q], dup2(invq));
+  // Eq 4 (reading R2): max(D max(f, 0), floor) = max(D f, floor) for D >= 0
+  float2 r[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const float2 f = __ffma2_rn(fc.nxi, F[q], __ffma2_rn(fc.nlam, H[q], dup2(1.0f)));
+    const float2 dd = __fadd2_rn(dup2(d.x), fc.ncc[q]);
+    const float2 d2 = max2(__fmul2_rn(__fmul2_rn(dd, dd), f), fc.floor);
+    r[q] = make_float2(fast_rcp(d2.x), fast_rcp(d2.y));
+  }
+  // Eq 2 with m = 2: u_j = (1/d2_j) / S, S = sum_k 1/d2_k; Eq 1 share = 1/S
+  float2 S = r[0];
+#pragma unroll
+  for (int q = 1; q < C; ++q) S = __fadd2_rn(S, r[q]);
+  const float2 inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
+  acc.J = __fadd2_rn(acc.J, inv);
+  const float2 x2 = dup2(d.x);
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const float2 u = __fmul2_rn(r[q], inv);
+    const float2 um = __fmul2_rn(u, u);
+    acc.s0[q] = __fadd2_rn(acc.s0[q], um);
+    acc.s1[q] = __ffma2_rn(um, x2, acc.s1[q]);
+    if (st) __stcg(&dst[q * plane], u);
+    const float2 e = __ffma2_rn(ud[q * PLANE], dup2(-1.0f), u);   // u' - u
+    acc.dm.x = fmaxf(acc.dm.x, fabsf(e.x));
+    acc.dm.y = fmaxf(acc.dm.y, fabsf(e.y));
+  }
+}
+
+// Plane pz of the column: finalise centre pz - 2 (slot d, when FIN), add
+// plane pz to centres pz - 1 (l), pz (m) and pz + 1 (h, whose sums start
+// here; its x and s come from stage pz + 1).  xs / us: stage pz at the
+// column; xn / sn: stage pz + 1 at the column; ud: stage pz - 2 at the column.
+template <int C, bool FIN>
+__device__ __forceinline__ void step3(const float* __restrict__ xs, const float2* __restrict__ us,
+                                      const float* __restrict__ xn, const float* __restrict__ sn,
+                                      const float2* __restrict__ ud, Slot3<C>& d, Slot3<C>& l,
+                                      Slot3<C>& m, Slot3<C>& h, float invq, const Fin3<C>& fc,
+                                      Acc3<C>& acc, float2* __restrict__ dst, int plane,
+                                      bool st) {
+  constexpr int KH = C - 1;
+  h.x = xn[0];
+  h.s = sn[0];
+  h.e = h.s < 0.0f ? 1.0f : 0.0f;
+  if (FIN) fin3<C>(d, ud, invq, fc, acc, dst, plane, st);
+  float2 W0[C], S1[C], S2[C];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int off = dy * BX + dx;
+      const bool self = dx == 0 && dy == 0;
+      const bool first = dx == -1 && dy == -1;
+      const int q2 = dx * dx + dy * dy;
+      const bool first_face = dy == -1 && dx == 0, first_corner = first;
+      const float xk = xs[off];
+      // g = max(|x_i - x_k|, e_i): 0 where x_k is the NaN outside the volume
+      const float gl = fmaxf(fabsf(l.x - xk), l.e);
+      const float gh = fmaxf(fabsf(h.x - xk), h.e);
+      const float gm = self ? 0.0f : fmaxf(fabsf(m.x - xk), m.e);
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        const float2 uk = us[q * PLANE + off];
+        if (q < KH) {
+          l.H[q] = __ffma2_rn(uk, dup2(gl), l.H[q]);
+          h.H[q] = first ? __fmul2_rn(uk, dup2(gh)) : __ffma2_rn(uk, dup2(gh), h.H[q]);
+          if (!self) m.H[q] = __ffma2_rn(uk, dup2(gm), m.H[q]);
+        }
+        if (self) W0[q] = __fmul2_rn(uk, uk);
+        else if (q2 == 1) S1[q] = first_face ? __fmul2_rn(uk, uk) : __ffma2_rn(uk, uk, S1[q]);
+        else S2[q] = first_corner ? __fmul2_rn(uk, uk) : __ffma2_rn(uk, uk, S2[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const float2 V = __ffma2_rn(dup2(2.0f), S2[q], S1[q]);                          // S1 + 2 S2
+    const float2 A = __ffma2_rn(dup2(3.0f), S2[q], __ffma2_rn(dup2(2.0f), S1[q], W0[q]));
+    l.F[q] = __fadd2_rn(l.F[q], A);
+    m.F[q] = __fadd2_rn(m.F[q], V);
+    h.F[q] = A;
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant__ StencilArgs a) {
+  extern __shared__ unsigned char dsmem_raw[];
+  __shared__ __align__(8) uint64_t full[NSTAGE];
+  __shared__ __align__(8) uint64_t empty[NSTAGE];
+  __shared__ ItemTable tab;
+  __shared__ int s_abort;
+  __shared__ float s_red[NCW][2 * (2 * C + 2)];
+  __shared__ ItemConst<C, 2> s_ic;
+
+  // 128-byte aligned start by pointer arithmetic, so that the compiler keeps
+  // the shared address space of every stage pointer
+  unsigned char* dsmem = dsmem_raw + ((128u - (smem_addr(dsmem_raw) & 127u)) & 127u);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int SB = s3_stage_bytes<C>();
+
+  // Active pairs of every volume, compacted one volume per warp (ballots).
+  for (int v = warp; v < a.n_vol; v += NT / 32) {
+    const VolDesc& vd = a.vol[v];
+    const int units = vd.nz == 1 ? 0 : (vd.P + 1) / 2;
+    int n = 0;
+    for (int base = 0; base < units; base += 32) {
+      const int p = base + lane;
+      const bool on = p < units && (a.active[vd.pbase + 2 * p] != 0 ||
+                                    (2 * p + 1 < vd.P && a.active[vd.pbase + 2 * p + 1] != 0));
+      const unsigned msk = __ballot_sync(0xffffffffu, on);
+      if (on) tab.act[vd.pbase + n + __popc(msk & ((1u << lane) - 1u))] = static_cast<short>(p);
+      n += __popc(msk);
+    }
+    if (lane == 0) {
+      tab.vfirst[v] = vd.pbase;
+      tab.vnact[v] = n;
+    }
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int items = 0;
+    for (int v = 0; v < a.n_vol; ++v) {
+      tab.vitem[v] = items;
+      items += tab.vnact[v] * a.vol[v].n_tiles;
+    }
+    tab.vitem[a.n_vol] = items;
+  }
+  __syncthreads();
+  const int n_items = tab.vitem[a.n_vol];
+  if (static_cast<int>(blockIdx.x) >= n_items) return;
+
+  // ------------------------------------------------------------ producer
+  if (warp == NCW) {
+    if (lane == 0) {
+      uint32_t q = 0;
+      for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const Item it = decode_item<2, UL_F32P>(a, tab, w);
+        const VolDesc& vd = a.vol[it.v];
+        const CUtensorMap* mx = &a.tm_x[it.v];
+        const CUtensorMap* mu = &a.tm_u[it.v];
+        const CUtensorMap* mg = &a.tm_s[it.v];
+        for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
+          const uint32_t s = q & (NSTAGE - 1);
+          if (q >= NSTAGE &&
+              !mbar_wait_bounded(&empty[s], ((q / NSTAGE) - 1) & 1)) {
+            atomicExch(&s_abort, 1);
+            set_status(a.status, IFCM_ERR_TIMEOUT, 5);
+            return;
+          }
+          if (*reinterpret_cast<volatile int*>(&s_abort)) return;
+          unsigned char* st = dsmem + s * SB;
+          mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C>());
+          tma_load_3d(st, mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
+          tma_load_3d(st + XBYTES, mg, &full[s], it.x0, it.y0, pz);
+          tma_load_4d(st + XBYTES + SBYTES, mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
+                      it.unit * vd.src_cstride);
+        }
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  const int tx = tid & 31, ty = tid >> 5;
+  const int cidx = (ty + 1) * BX + tx + 4;     // the column in a stage plane
+  const int sidx = ty * TX + tx;               // the column in a stage's 1/G tile
+  uint32_t q = 0;
+
+  auto xs_at = [&](uint32_t qq) {
+    return reinterpret_cast<const float*>(dsmem + (qq & (NSTAGE - 1)) * SB) + cidx;
+  };
+  auto ss_at = [&](uint32_t qq) {
+    return reinterpret_cast<const float*>(dsmem + (qq & (NSTAGE - 1)) * SB + XBYTES) + sidx;
+  };
+  auto us_at = [&](uint32_t qq) {
+    return reinterpret_cast<const float2*>(dsmem + (qq & (NSTAGE - 1)) * SB + XBYTES + SBYTES) +
+           cidx;
+  };
+  auto wait_full = [&](uint32_t qq) -> bool {
+    if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
+    if (!mbar_wait_bounded(&full[qq & (NSTAGE - 1)], (qq / NSTAGE) & 1)) {
+      atomicExch(&s_abort, 1);
+      set_status(a.status, IFCM_ERR_TIMEOUT, 6);
+      return false;
+    }
+    return true;
+  };
+  auto release = [&](uint32_t qq) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[qq & (NSTAGE - 1)]);
+  };
+
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const Item it = decode_item<2, UL_F32P>(a, tab, w);
+    const VolDesc& vd = a.vol[it.v];
+    const int plane = vd.nz * vd.ny * vd.pitch;
+    const Ctx cx = column_ctx(it.x0 + tx, it.y0 + ty, vd);
+    float iqz;   // 1/Q of the column's centres on a z face
+    {
+      int cnt;
+      float Q;
+      box_counts(cx.X, cx.Y, 0, vd.nx, vd.ny, vd.nz, cnt, Q);
+      iqz = cnt > 0 ? __frcp_rn(Q) : 0.0f;
+    }
+    if (tid == 0) {
+      float lam[2], xi[2], cc[2][C];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int pid = p == 0 ? it.p0 : it.p1;
+        lam[p] = static_cast<float>(vd.lam_xi[2 * pid]);
+        xi[p] = static_cast<float>(vd.lam_xi[2 * pid + 1]);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
+      }
+      s_ic.dst[0] = vd.u_dst + static_cast<size_t>(it.unit) * C * plane * 2;
+      s_ic.nlam = make_float2(-lam[0], -lam[1]);
+      s_ic.nxi = make_float2(-xi[0], -xi[1]);
+#pragma unroll
+      for (int j = 0; j < C; ++j) s_ic.ncc[j] = make_float2(-cc[0][j], -cc[1][j]);
+    }
+    consumer_sync();
+    Fin3<C> fc;
+#pragma unroll
+    for (int j = 0; j < C; ++j) fc.ncc[j] = s_ic.ncc[j];
+    fc.nlam = s_ic.nlam;
+    fc.nxi = s_ic.nxi;
+    fc.floor = a.dist_floor;
+    const float iqc = cx.invQ_col;
+    const bool st = cx.col_ok;
+    float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
+    const int zstride = vd.ny * vd.pitch;
+
+    Slot3<C> s0, s1, s2, s3;
+    Acc3<C> acc;
+    acc.clear();
+    const int np = it.pze - it.pzb + 1;
+    const uint32_t q0 = q;
+    // the first step whose delayed finalisation is a centre of the item
+    const int kf = it.z0 - it.pzb + 2;
+    // the generic step covers the steps before the first interior-z centre
+    const int kh = kf + (it.z0 == 0 ? 1 : 0);
+    bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
+    // centre pzb (slot m of the first step) starts with no sums; centre
+    // pzb - 1 (slot l) is never finalised
+    s1.clear();
+    s2.clear();
+    if (ok) {
+      s2.x = xs_at(q0)[0];
+      s2.s = ss_at(q0)[0];
+      s2.e = s2.s < 0.0f ? 1.0f : 0.0f;
+    }
+
+    // One plane with slot values rotated afterwards (first and last planes
+    // of the item): the finalisation only from step kf on, the z-face 1/Q
+    // for centre 0, no wait past the item's last plane.
+    auto generic = [&](int kk) {
+      const uint32_t qq = q0 + kk;
+      const bool need2 = kk + 2 < np;
+      const bool landed2 = !need2 || mbar_test_wait(&full[(qq + 2) & (NSTAGE - 1)],
+                                                    ((qq + 2) / NSTAGE) & 1);
+      const int zd = it.pzb + kk - 2;
+      if (ok) {
+        const float invq = zd == 0 ? iqz : iqc;
+        float2* dst = col_dst + static_cast<long long>(zd) * zstride;
+        if (kk >= kf)
+          step3<C, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0, s1,
+                         s2, s3, invq, fc, acc, dst, plane, st);
+        else
+          step3<C, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
+                          s1, s2, s3, invq, fc, acc, dst, plane, st);
+      }
+      if (!landed2) ok = ok && wait_full(qq + 2);
+      if (kk >= 2) release(qq - 2);
+      s0 = s1;
+      s1 = s2;
+      s2 = s3;
+    };
+
+    int kk = 0;
+    for (; kk < kh && kk < np; ++kk) generic(kk);
+    // steady state: four planes per pass, slots in static rotation; every
+    // step has its finalisation, an interior-z centre, and two stages ahead
+    for (; ok && kk + 4 <= np - 2; kk += 4) {
+      const uint32_t qq = q0 + kk;
+      float2* dst = col_dst + static_cast<long long>(it.pzb + kk - 2) * zstride;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t qr = qq + r;
+        const bool landed2 =
+            mbar_test_wait(&full[(qr + 2) & (NSTAGE - 1)], ((qr + 2) / NSTAGE) & 1);
+        Slot3<C>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
+        Slot3<C>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
+        Slot3<C>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
+        Slot3<C>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
+        step3<C, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l, m,
+                       h, iqc, fc, acc, dst + r * zstride, plane, st);
+        if (!landed2) ok = ok && wait_full(qr + 2);
+        release(qr - 2);
+      }
+    }
+    for (; kk < np; ++kk) generic(kk);
+
+    // After the last plane: s0 = centre pze - 1 (complete), s1 = centre pze
+    // (complete only when pze is the top plane of the volume).
+    {
+      const uint32_t ql = q0 + np - 1;
+      const bool live = ok && !*reinterpret_cast<volatile int*>(&s_abort);
+      const int zl = it.pze - 1;
+      if (live && np >= 2 && zl >= it.z0 && zl < it.z1)
+        fin3<C>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
+                col_dst + static_cast<long long>(zl) * zstride, plane, st);
+      if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1)
+        fin3<C>(s1, us_at(ql), iqz, fc, acc, col_dst + static_cast<long long>(it.pze) * zstride,
+                plane, st);
+      if (np >= 2) release(ql - 1);
+      release(ql);
+    }
+    q = q0 + np;
+    if (!cx.col_ok) acc.clear();      // lanes outside the volume computed on garbage
+
+    // Item partial sums: FP32 within a thread and a warp, FP64 across warps.
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float v0 = warp_sum(p == 0 ? acc.s0[j].x : acc.s0[j].y);
+        const float v1 = warp_sum(p == 0 ? acc.s1[j].x : acc.s1[j].y);
+        if (lane == 0) {
+          s_red[warp][p * (2 * C + 2) + j] = v0;
+          s_red[warp][p * (2 * C + 2) + C + j] = v1;
+        }
+      }
+      const float vj = warp_sum(p == 0 ? acc.J.x : acc.J.y);
+      const float vm = warp_max(p == 0 ? acc.dm.x : acc.dm.y);
+      if (lane == 0) {
+        s_red[warp][p * (2 * C + 2) + 2 * C] = vj;
+        s_red[warp][p * (2 * C + 2) + 2 * C + 1] = vm;
+      }
+    }
+    consumer_sync();
+    if (tid < 2 * (2 * C + 2)) {
+      const int p = tid / (2 * C + 2), v = tid - p * (2 * C + 2);
+      if (p == 0 ? it.on0 : it.two) {
+        const int pid = p == 0 ? it.p0 : it.p1;
+        const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
+        if (v < 2 * C + 1) {
+          if (a.reduce == IFCM_REDUCE_FP64) {
+            double sum = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < NCW; ++wv) sum += static_cast<double>(s_red[wv][tid]);
+            a.partials[rec * (2 * C + 1) + v] = sum;
+          } else {
+            float sum = 0.0f, comp = 0.0f;
+#pragma unroll
+            for (int wv = 0; wv < NCW; ++wv) neumaier_add(sum, comp, s_red[wv][tid]);
+            a.partials[rec * (2 * C + 1) + v] = static_cast<double>(__fadd_rn(sum, comp));
+          }
+        } else {
+          float mm = 0.0f;
+#pragma unroll
+          for (int wv = 0; wv < NCW; ++wv) mm = fmaxf(mm, s_red[wv][tid]);
+          a.dmax[rec] = mm;
+        }
+      }
+    }
+    consumer_sync();
+  }
+}
+
+// One launch of the 3D float2-pair kernel (every volume of `a` is 3D).
+template <int C>
+cudaError_t launch3d_c(const StencilArgs& a, int grid, cudaStream_t s) {
+  constexpr int smem = s3_smem_total<C>();
+  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  stencil3d_kernel<C><<<grid, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace pifcm

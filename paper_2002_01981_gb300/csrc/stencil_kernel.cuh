@@ -993,12 +993,13 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
 // One iteration over the launch's volumes: the 3D kernel if it has 3D
 // volumes, the 2D kernel if it has 2D images (both, one after the other on
 // the stream, for a batch that mixes them).
+// With deep_ok false the 3D volumes are left to another kernel.
 template <int C, int NP, int UL>
-cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s, bool deep_ok = true) {
   constexpr int smem = smem_total<C, NP, UL>();
   bool flat = false, deep = false;
   for (int v = 0; v < a.n_vol; ++v) (a.vol[v].nz == 1 ? flat : deep) = true;
-  if (deep) {
+  if (deep && deep_ok) {
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -163,12 +163,13 @@ def _storage_rounding_floor(x, U, C, lam, xi, iters):
 
 def u_bound(x, U, C, lam, xi, iters):
     """U tolerance of a run: 1e-5, except in the clamp regime (lambda + xi > 1,
-    reading R2 of Eq 4) where it is ten times the oracle's own FP32-storage
-    sensitivity (the FP32 arithmetic inside an iteration rounds ~10x more
-    often than storage alone)."""
+    reading R2 of Eq 4), where it is four times the oracle's own FP32-storage
+    sensitivity.  The GPU's U error was measured at 1.2 to 3.0 times that
+    sensitivity on test_clamp_regime_runs' cases and at (0.5, 0.4), (0.3,
+    0.3)."""
     if lam + xi <= 1.0:
         return U_TOL
-    return max(U_TOL, 10.0 * _storage_rounding_floor(x, U, C, lam, xi, iters))
+    return max(U_TOL, 4.0 * _storage_rounding_floor(x, U, C, lam, xi, iters))
 
 
 @pytest.mark.parametrize("lam,xi", [(0.9, 0.8), (1.0, 1.0), (0.7, 0.6)])
@@ -414,8 +415,7 @@ def test_fitness_multi_equals_single_volume_runs(G, eps):
     prm = G.Params(max_iter=12, eps_u=eps)
     outs = G.pso_fitness_multi(vols, prm)
     for v, (fit, its) in zip(vols, outs):
-        pc = G.Params(c=v.c, max_iter=12, eps_u=eps)
-        f1, i1, _ = G.pso_fitness_batch(v.x, pc, v.lam_xi, v.u0, v.c0, nx=v.nx)
+        f1, i1 = _single_call(G, v, G.Params(c=v.c, max_iter=12, eps_u=eps))
         # same arithmetic per (particle, tile) and a fixed reduction order
         assert _same_fitness(fit, f1, len(fit), flat=v.x.shape[0] == 1)
         assert torch.equal(its, i1)
@@ -444,18 +444,29 @@ def test_fitness_multi_in_workspace_sized_waves(G):
 
 
 def _same_fitness(fit, f1, P, flat=False):
-    """Multi-volume fitness against the single-volume call.  Bit-equal when
-    both launches cut the volume alike.  Two cases cut it differently, and the
-    FP32 rounding-order difference is carried through the iterations, so they
-    use the J bar (1e-5 relative):
-    - a volume with one particle runs alone with its clusters paired in the
-      packed lanes (pairs (0,1), (2,3)), so the m = 2 denominator sums as
-      (r0 + r1) + (r2 + r3) instead of ((r0 + r1) + r2) + r3;
-    - a 2D image (flat) is cut into runs of tiles whose length follows the
-      launch's plan, and a thread's FP32 sums run over its run of tiles."""
-    if P == 1 or flat:
+    """Multi-volume fitness against the single-volume call (_single_call).
+    Bit-equal when both launches cut the volume alike.  A 2D image (flat) is
+    cut into runs of tiles whose length follows the launch's plan, and a
+    thread's FP32 sums run over its run of tiles, so it uses the J bar (1e-5
+    relative)."""
+    if flat:
         return torch.allclose(fit, f1, rtol=J_RTOL, atol=0)
     return torch.equal(fit, f1)
+
+
+def _single_call(G, v, prm):
+    """The single-volume call a multi-volume volume is compared with.  In a
+    multi-volume launch a volume's particles run in pairs; a lone particle
+    shares its pair with a copy of itself.  So a one-particle volume is
+    compared with a two-particle call on two copies of it, which runs the same
+    kernel with the same arithmetic, not with a one-particle call (a different
+    kernel, with its clusters paired in the packed lanes)."""
+    lx = np.asarray(v.lam_xi, np.float64).reshape(-1, 2)
+    if len(lx) == 1:
+        lx = np.concatenate([lx, lx])
+    f1, i1, _ = G.pso_fitness_batch(v.x, prm, lx, v.u0, v.c0, nx=v.nx)
+    n = len(np.asarray(v.lam_xi).reshape(-1, 2))
+    return f1[:n], i1[:n]
 
 
 def test_fitness_multi_beyond_one_launch(G):
@@ -466,8 +477,7 @@ def test_fitness_multi_beyond_one_launch(G):
     prm = G.Params(max_iter=4, eps_u=0.0)
     outs = G.pso_fitness_multi(vols, prm)
     for v, (fit, its) in zip(vols, outs):
-        f1, i1, _ = G.pso_fitness_batch(v.x, G.Params(c=v.c, max_iter=4, eps_u=0.0), v.lam_xi,
-                                        v.u0, v.c0, nx=v.nx)
+        f1, i1 = _single_call(G, v, G.Params(c=v.c, max_iter=4, eps_u=0.0))
         assert _same_fitness(fit, f1, len(fit), flat=v.x.shape[0] == 1) and torch.equal(its, i1)
     big = [((4, 6, 8), 3, 1000), ((5, 5, 9), 3, 1000), ((6, 4, 7), 3, 1000),
            ((3, 7, 8), 3, 1000), ((4, 4, 4), 3, 1000)]
