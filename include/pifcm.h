@@ -406,7 +406,26 @@ ifcm_status ifcm_profile_read(double* kernel_ms, int64_t* launches);
 #define IFCM_PROF_STENCIL 0
 #define IFCM_PROF_ADJOINT_POINT 1
 #define IFCM_PROF_ADJOINT_GATHER 2
+/* IFCM_PROF_STENCIL3D: the stencil iterations of batches of 3D volumes that
+ * run the float2-pair plane step alone (every iteration after the first of
+ * an FP32 batch of two or more particles with m = 2, c <= 5); they are
+ * counted in IFCM_PROF_STENCIL as well. */
+#define IFCM_PROF_STENCIL3D 3
 ifcm_status ifcm_profile_read_kind(int32_t kind, double* kernel_ms, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
+ * Failure detection.  Every wait of a kernel on the arrival of its
+ * shared-memory tiles (an mbarrier phase) is bounded: after ns nanoseconds
+ * of the GPU's global timer without the phase completing, the kernel records
+ * IFCM_ERR_TIMEOUT in the workspace's status word (ifcm_device_status), stops
+ * issuing copies, waits (bounded, about a second) for the copies it already
+ * issued, and returns; later launches of the call see the status and the
+ * host entry points return normally.  The setting is process-wide and read
+ * when a call builds its launches; 0 (the default) bounds each wait at about
+ * one second.  A bound below 1000 ns gives up at the first unsuccessful
+ * non-blocking test of a phase, which makes waits run out on purpose (for
+ * tests of this path); they leave the GPU context usable. */
+void ifcm_set_wait_limit_ns(uint64_t ns);
 
 #ifdef __cplusplus
 }

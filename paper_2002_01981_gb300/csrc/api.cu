@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -290,10 +291,10 @@ constexpr cuuint32_t kBoxX = kTX + 8, kBoxY = kTY + 2;
 // planes <= 0: the volume x; else a membership map of `planes` planes of
 // elem_bytes-byte elements (4: FP32 or a bf16x2 word; 8: a float2 word).
 ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int planes,
-                     int box_planes, int elem_bytes = 4) {
+                     int box_planes, int elem_bytes = 4, bool nan_fill = true) {
   ST_TRY(get_encode());
   const cuuint64_t row = static_cast<cuuint64_t>(s.pitch_x) * (planes <= 0 ? 4 : elem_bytes);
-  if (planes <= 0) {   // 3D volume map: positions outside the volume read as NaN
+  if (planes <= 0) {   // 3D volume map: positions outside the volume read as NaN (or 0)
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(s.nx), static_cast<cuuint64_t>(s.ny),
                           static_cast<cuuint64_t>(s.nz)};
     cuuint64_t strides[2] = {row, row * s.ny};
@@ -302,7 +303,8 @@ ifcm_status make_map(CUtensorMap* m, const float* base, const ifcm_shape& s, int
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
+                          nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA
+                                   : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(IFCM_ERR_CUDA, "tensor map (volume) failed: %d", (int)r);
     return IFCM_OK;
   }
@@ -347,12 +349,14 @@ int sm_count() {
 }
 
 // ------------------------------------------------------------ profiling
-// Event pairs around kernel launches of three kinds (IFCM_PROF_*): the
-// stencil iteration, the adjoint point kernel and the adjoint gather kernel.
+// Event pairs around kernel launches of four kinds (IFCM_PROF_*): the
+// stencil iteration, the adjoint point kernel, the adjoint gather kernel, and
+// the stencil iterations of 3D batches that run stencil3d_kernel alone (those
+// launches are in the first kind as well).
 struct Profiler {
   std::mutex mu;
   bool on = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used[3];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used[4];
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
 } g_prof;
 
@@ -473,6 +477,9 @@ std::vector<long long> plan_key(const BatchVol* vols, int n, int c, int u_dtype)
 
 // Parameter block of one iteration kind: 0 reads the shared start U0 and
 // writes ua, 1 reads ua and writes ub, 2 reads ub and writes ua.
+// Bound of every mbarrier wait of the stencil kernels (ifcm_set_wait_limit_ns).
+std::atomic<unsigned long long> g_wait_ns{0};
+
 ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_params* p,
                        const RunBufs& rb, const StencilPlan& pl, int kind, DevStatus* status) {
   const int c = p->c;
@@ -484,6 +491,7 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
   a.dmax = rb.dmax;
   a.status = status;
   a.sum_one = kind != 0;   // later iterations read Eq 2's memberships
+  a.wait_ns = g_wait_ns.load();
   fill_method(a, p);
   for (int v = 0; v < n; ++v) {
     const BatchVol& bv = vols[v];
@@ -504,7 +512,8 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.rec_base = rb.rec_base[v];
     d.lam_xi = bv.lam_xi;
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
-    ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0));
+    const bool k3 = stencil3d_eligible(rb.layout, pl.np, a.m_is_2, a.sum_one, s.nz);
+    ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0, 4, !k3));
     ST_TRY(make_smap(&a.tm_s[v], rb.gs[v], s));
     if (rb.layout != UL_PLANAR) {
       // pair words: K planes per unit (a particle pair for np = 2, a particle
@@ -705,9 +714,15 @@ struct BatchRun {
     const int c = p->c;
     const int kind = it == 0 ? 0 : (it % 2 == 1 ? 1 : 2);
     if (!wide) {
-      cudaEvent_t ev_end = nullptr;
+      bool k3 = true;   // the launch is one stencil3d_kernel launch
+      for (int v = 0; v < n; ++v)
+        k3 = k3 && stencil3d_eligible(rb->layout, pl.np, args[kind].m_is_2, args[kind].sum_one,
+                                      vols[v].shape.nz);
+      cudaEvent_t ev_end = nullptr, ev3_end = nullptr;
       cudaEvent_t ev_beg = prof_begin(st, &ev_end);
+      cudaEvent_t ev3_beg = k3 ? prof_begin(st, &ev3_end, IFCM_PROF_STENCIL3D) : nullptr;
       CU_TRY(launch_stencil(c, pl.np, rb->layout, args[kind], grid, st));
+      if (ev3_beg) cudaEventRecord(ev3_end, st);
       if (ev_beg) cudaEventRecord(ev_end, st);
     } else {
       for (int v = 0; v < n; ++v) {
@@ -1528,6 +1543,8 @@ ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_par
   return IFCM_OK;
 }
 
+void ifcm_set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns); }
+
 // ------------------------------------------------------------ profiling
 void ifcm_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -1535,7 +1552,7 @@ void ifcm_profile_enable(int32_t on) {
 }
 
 ifcm_status ifcm_profile_read_kind(int32_t kind, double* kernel_ms, int64_t* launches) {
-  if (kind < 0 || kind > 2) return fail(IFCM_ERR_INVALID, "profile kind %d outside 0..2", kind);
+  if (kind < 0 || kind > 3) return fail(IFCM_ERR_INVALID, "profile kind %d outside 0..3", kind);
   std::lock_guard<std::mutex> lk(g_prof.mu);
   double total = 0.0;
   auto& used = g_prof.used[kind];

@@ -154,9 +154,12 @@ __global__ void unpack_select_kernel(const W* a, const W* b, const int32_t* iter
 }
 
 // 1/G of every voxel of a 3D volume (G = sum over the in-volume neighbours of
-// |x_i - x_k|, Eqs 5-6; reading R4), summed in FP64 and rounded once; a flat
-// neighbourhood (G = 0, reading R3) is stored as -1/n (n in-volume
-// neighbours), and a G below FP32's range as the largest float.
+// |x_i - x_k|, Eqs 5-6; reading R4), summed in FP64 and rounded once; a G
+// below FP32's range is stored as the largest float.  A flat neighbourhood
+// (G = 0, reading R3) is stored as -1/(n g0), n its in-volume neighbours:
+// stencil3d_kernel weighs every neighbour of such a voxel with g0 =
+// |(x_i + 2) - x_k| = |(x_i + 2) - x_i| in FP32 (the same for all of them),
+// which turns H into the plain mean of the neighbours' memberships.
 __global__ void gsum_kernel(const float* __restrict__ x, int nx, int ny, int nz, int pitch,
                             float* __restrict__ out) {
   const long long n = static_cast<long long>(nx) * ny * nz;
@@ -181,7 +184,12 @@ __global__ void gsum_kernel(const float* __restrict__ x, int nx, int ny, int nz,
         }
     float s;
     if (G > 0.0) s = static_cast<float>(fmin(1.0 / G, 3.4028234663852886e38));
-    else s = cnt > 0 ? -1.0f / static_cast<float>(cnt) : 0.0f;
+    else if (cnt > 0) {
+      const float g0 = fabsf(__fsub_rn(__fadd_rn(xi, 2.0f), xi));
+      s = static_cast<float>(-1.0 / (static_cast<double>(cnt) * g0));
+    } else {
+      s = 0.0f;
+    }
     out[(static_cast<long long>(Z) * ny + Y) * pitch + X] = s;
   }
 }

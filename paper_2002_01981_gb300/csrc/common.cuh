@@ -82,14 +82,19 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Default bound of a wait: about one second.
 constexpr uint64_t kWaitLimitNs = 1ull << 30;
+// Bounds below this give up at the first unsuccessful non-blocking test
+// (the global timer ticks more coarsely than that).
+constexpr uint64_t kWaitImmediateNs = 1000;
 
-// Bounded wait on one phase of an mbarrier.  After limit_ns nanoseconds of
-// %globaltimer without the phase completing, the wait gives up and returns
-// false, so that the caller can record IFCM_ERR_TIMEOUT and leave instead of
-// spinning forever.  A limit of 0 gives up at the first unsuccessful try.
+// Bounded wait on one phase of an mbarrier: a non-blocking test, then
+// try_waits (each may suspend the thread for a while) until limit_ns
+// nanoseconds of %globaltimer have passed without the phase completing.  It
+// then gives up and returns false, so that the caller can record
+// IFCM_ERR_TIMEOUT and leave instead of spinning forever.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns = kWaitLimitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit_ns < kWaitImmediateNs) return false;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;

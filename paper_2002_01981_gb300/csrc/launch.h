@@ -55,6 +55,7 @@ struct StencilArgs {
   int m_is_2;
   int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across warps
   int sum_one;                  // U^t comes from Eq 2 (memberships of a voxel sum to one)
+  unsigned long long wait_ns;   // bound of one mbarrier wait (0: about one second)
   DevStatus* status;
 };
 static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay below 32 KB");
@@ -62,6 +63,14 @@ static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay be
 // Layout of the memberships between iterations (see stencil_kernel.cuh):
 // FP32 planes per particle, bf16 pair words, or float2 pair words.
 constexpr int UL_PLANAR = 0, UL_BF16 = 1, UL_F32P = 2;
+
+// Whether a volume of a stencil launch runs stencil3d_kernel: 3D, float2 pair
+// words with two particles per item, m = 2, and U^t from Eq 2 (every iteration
+// after the first).  Its volume map is zero-filled outside the volume; the
+// other kernels' maps are NaN-filled.
+inline bool stencil3d_eligible(int layout, int np, int m_is_2, int sum_one, int nz) {
+  return layout == UL_F32P && np == 2 && m_is_2 && sum_one && nz > 1;
+}
 
 // np = particles sharing one work item: 1 for every c, 2 for c <= 5.
 bool stencil_np_supported(int c, int np);

@@ -14,12 +14,15 @@
 //
 // - G_i = sum_k g_ik does not change between iterations (x is fixed), so it is
 //   computed once per volume (gsum_kernel, in FP64) and stored as s_i = 1/G_i.
-//   A flat neighbourhood (G_i = 0, reading R3) is stored as s_i = -1/n_i with
-//   n_i its in-volume neighbours: the stencil then takes g_ik = max(|x_i -
-//   x_k|, e_i) with e_i = 1 for such a voxel and 0 otherwise, which gives
-//   every in-volume neighbour weight 1 and turns H into the plain mean, with
-//   no branch.  (Out-of-volume neighbours hold u = 0, so their weight never
-//   counts, and |s_i| = 1/n_i divides by the in-volume count.)
+// - Neighbours outside the volume need no mask or max: the volume's tensor
+//   map fills them with x = 0 and the membership maps with u = 0, so their
+//   products u_kj g_ik vanish (reading R4), and G excludes them.  g_ik =
+//   |x_i - x_k| costs one FADD, the absolute value being an operand modifier
+//   of the packed FMA that uses it.
+// - A flat neighbourhood (G_i = 0, reading R3) is stored as s_i = -1/(n_i g0)
+//   with n_i its in-volume neighbours, and its centre value in the g_ik is
+//   x_i + 2: every in-volume neighbour then has the same weight g0 = |(x_i +
+//   2) - x_i|, which turns H into the plain mean, with no branch.
 // - Memberships of one voxel sum to one (Eq 2), so sum_j H_ij = 1 and the last
 //   cluster's H is 1 - sum_{j<c-1} H_ij: its 26 neighbour products are not
 //   formed.  U^t always comes from Eq 2 here (iteration 0, which reads the
@@ -30,7 +33,7 @@
 //   above and below) and V = S1 + 2 S2 (weight dx^2 + dy^2, to the centre in
 //   the plane).
 // - No warp votes or branches in the plane step: out-of-volume lanes of an
-//   overhanging tile compute on (x reads NaN there) but their stores are
+//   overhanging tile compute on (on x = 0) but their stores are
 //   predicated off and their sums are zeroed once per item; the z-face
 //   centres differ only in 1/Q, a step argument.
 // - The four centre slots change roles, not values: the steady-state loop is
@@ -71,14 +74,14 @@ struct Slot3 {
   float2 H[KH];                      // sum_k u_kj g_ik, pair = the item's two particles
   float2 F[C];                       // sum_k u_kj^2 q^2_ik
   float x;                           // x_i
-  float s;                           // 1/G_i, or -1/n_i for a flat neighbourhood
-  float e;                           // floor of g_ik: 1 for a flat neighbourhood, else 0
+  float s;                           // 1/G_i, or -1/(n_i g0) for a flat neighbourhood
+  float xg;                          // x_i in g_ik: x_i, or x_i + 2 for a flat neighbourhood
   __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int q = 0; q < KH; ++q) H[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < C; ++q) F[q] = make_float2(0.0f, 0.0f);
-    x = s = e = 0.0f;
+    x = s = xg = 0.0f;
   }
 };
 
@@ -101,30 +104,34 @@ struct Acc3 {
   }
 };
 
-// Finalise centre d: Eqs 5 and 7 (1/G from s, the last cluster's H by
-// complement), Eq 4 with reading R2, Eq 2 for m = 2, the U^{t+1} store and
-// the centre's shares of Eqs 1 and 3 and of max|du|.  ud: the centre's U^t
-// in its stage (pair words at its column); dst: its U^{t+1} word of pair 0.
+// Finalise centre d: Eqs 5 and 7 folded into the factor of Eq 4 (1/G from s,
+// 1/Q from invq, the last cluster's H by complement), Eq 4 with reading R2,
+// Eq 2 for m = 2, the U^{t+1} store and the centre's shares of Eqs 1 and 3
+// and of max|du|.  ud: the centre's U^t in its stage (pair words at its
+// column); dst: its U^{t+1} word of pair 0.
 template <int C>
 __device__ __forceinline__ void fin3(const Slot3<C>& d, const float2* __restrict__ ud, float invq,
                                      const Fin3<C>& fc, Acc3<C>& acc, float2* __restrict__ dst,
                                      int plane, bool st) {
   constexpr int KH = C - 1;
   const float ig = fabsf(d.s);
-  float2 H[C], F[C];
   float2 hs = d.H[0];
 #pragma unroll
   for (int q = 1; q < KH; ++q) hs = __fadd2_rn(hs, d.H[q]);
+  // f_j = 1 - lambda H_j - xi F_j with H_j = Hs_j / G and F_j = Fs_j / Q,
+  // taking -lambda / G and -xi / Q once per centre
+  const float2 nl = __fmul2_rn(fc.nlam, dup2(ig)), nx = __fmul2_rn(fc.nxi, dup2(invq));
+  float2 fq[C];
 #pragma unroll
-  for (int q = 0; q < KH; ++q) H[q] = __fmul2_rn(d.H[q], dup2(ig));
-  H[C - 1] = __ffma2_rn(hs, dup2(-ig), dup2(1.0f));          // 1 - sum_{j<c-1} H_j
-#pragma unroll
-  for (int q = 0; q < C; ++q) F[q] = __fmul2_rn(d.F[q], dup2(invq));
+  for (int q = 0; q < KH; ++q) fq[q] = __ffma2_rn(nx, d.F[q], __ffma2_rn(nl, d.H[q], dup2(1.0f)));
+  // the last cluster: 1 - lambda (1 - sum_{j<c-1} H_j) - xi F
+  fq[C - 1] = __ffma2_rn(nx, d.F[C - 1], __ffma2_rn(__fmul2_rn(nl, dup2(-1.0f)), hs,
+                                                    __fadd2_rn(dup2(1.0f), fc.nlam)));
   // Eq 4 (reading R2): max(D max(f, 0), floor) = max(D f, floor) for D >= 0
   float2 r[C];
 #pragma unroll
   for (int q = 0; q < C; ++q) {
-    const float2 f = __ffma2_rn(fc.nxi, F[q], __ffma2_rn(fc.nlam, H[q], dup2(1.0f)));
+    const float2 f = fq[q];
     const float2 dd = __fadd2_rn(dup2(d.x), fc.ncc[q]);
     const float2 d2 = max2(__fmul2_rn(__fmul2_rn(dd, dd), f), fc.floor);
     r[q] = make_float2(fast_rcp(d2.x), fast_rcp(d2.y));
@@ -163,7 +170,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
   constexpr int KH = C - 1;
   h.x = xn[0];
   h.s = sn[0];
-  h.e = h.s < 0.0f ? 1.0f : 0.0f;
+  h.xg = h.s < 0.0f ? h.x + 2.0f : h.x;
   if (FIN) fin3<C>(d, ud, invq, fc, acc, dst, plane, st);
   float2 W0[C], S1[C], S2[C];
 #pragma unroll
@@ -176,10 +183,9 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
       const int q2 = dx * dx + dy * dy;
       const bool first_face = dy == -1 && dx == 0, first_corner = first;
       const float xk = xs[off];
-      // g = max(|x_i - x_k|, e_i): 0 where x_k is the NaN outside the volume
-      const float gl = fmaxf(fabsf(l.x - xk), l.e);
-      const float gh = fmaxf(fabsf(h.x - xk), h.e);
-      const float gm = self ? 0.0f : fmaxf(fabsf(m.x - xk), m.e);
+      const float gl = fabsf(l.xg - xk);
+      const float gh = fabsf(h.xg - xk);
+      const float gm = self ? 0.0f : fabsf(m.xg - xk);
 #pragma unroll
       for (int q = 0; q < C; ++q) {
         const float2 uk = us[q * PLANE + off];
@@ -208,6 +214,7 @@ template <int C>
 __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant__ StencilArgs a) {
   extern __shared__ unsigned char dsmem_raw[];
   __shared__ __align__(8) uint64_t full[NSTAGE];
+  __shared__ uint32_t lastq[NSTAGE];    // the last plane loaded into each stage
   __shared__ __align__(8) uint64_t empty[NSTAGE];
   __shared__ ItemTable tab;
   __shared__ int s_abort;
@@ -220,6 +227,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   constexpr int SB = s3_stage_bytes<C>();
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   // Active pairs of every volume, compacted one volume per warp (ballots).
   for (int v = warp; v < a.n_vol; v += NT / 32) {
@@ -243,6 +251,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
     s_abort = 0;
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
+      lastq[s] = 0xffffffffu;
       mbar_init(&empty[s], NCW);
     }
     fence_mbarrier_init();
@@ -260,35 +269,43 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   const int n_items = tab.vitem[a.n_vol];
   if (static_cast<int>(blockIdx.x) >= n_items) return;
 
+  // One plane of an item into its ring stage (plane qq of the CTA's sequence).
+  auto load_plane = [&](uint32_t qq, const Item& it, int pz) {
+    const VolDesc& vd = a.vol[it.v];
+    const uint32_t s = qq & (NSTAGE - 1);
+    unsigned char* st = dsmem + s * SB;
+    lastq[s] = qq;
+    mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C>());
+    tma_load_3d(st, &a.tm_x[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz);
+    tma_load_3d(st + XBYTES, &a.tm_s[it.v], &full[s], it.x0, it.y0, pz);
+    tma_load_4d(st + XBYTES + SBYTES, &a.tm_u[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz,
+                it.unit * vd.src_cstride);
+  };
+
+
   // ------------------------------------------------------------ producer
   if (warp == NCW) {
     if (lane == 0) {
       uint32_t q = 0;
-      for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+      bool go = true;
+      for (int w = blockIdx.x; go && w < n_items; w += gridDim.x) {
         const Item it = decode_item<2, UL_F32P>(a, tab, w);
-        const VolDesc& vd = a.vol[it.v];
-        const CUtensorMap* mx = &a.tm_x[it.v];
-        const CUtensorMap* mu = &a.tm_u[it.v];
-        const CUtensorMap* mg = &a.tm_s[it.v];
         for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
           const uint32_t s = q & (NSTAGE - 1);
-          if (q >= NSTAGE &&
-              !mbar_wait_bounded(&empty[s], ((q / NSTAGE) - 1) & 1)) {
+          if (q >= NSTAGE && !mbar_wait_bounded(&empty[s], ((q / NSTAGE) - 1) & 1, wait_ns)) {
             atomicExch(&s_abort, 1);
             set_status(a.status, IFCM_ERR_TIMEOUT, 5);
-            return;
+            go = false;
+            break;
           }
-          if (*reinterpret_cast<volatile int*>(&s_abort)) return;
-          unsigned char* st = dsmem + s * SB;
-          mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C>());
-          tma_load_3d(st, mx, &full[s], it.x0 - 4, it.y0 - 1, pz);
-          tma_load_3d(st + XBYTES, mg, &full[s], it.x0, it.y0, pz);
-          tma_load_4d(st + XBYTES + SBYTES, mu, &full[s], it.x0 - 4, it.y0 - 1, pz,
-                      it.unit * vd.src_cstride);
+          if (*reinterpret_cast<volatile int*>(&s_abort)) {
+            go = false;
+            break;
+          }
+          load_plane(q, it, pz);
         }
       }
     }
-    return;
   }
 
   // ------------------------------------------------------------ consumers
@@ -309,30 +326,28 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   };
   auto wait_full = [&](uint32_t qq) -> bool {
     if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
-    if (!mbar_wait_bounded(&full[qq & (NSTAGE - 1)], (qq / NSTAGE) & 1)) {
+    const bool landed = mbar_wait_bounded(&full[qq & (NSTAGE - 1)], (qq / NSTAGE) & 1, wait_ns);
+    if (!landed) {
       atomicExch(&s_abort, 1);
       set_status(a.status, IFCM_ERR_TIMEOUT, 6);
       return false;
     }
     return true;
   };
+
+  // stage qq is free once every consumer warp released it
   auto release = [&](uint32_t qq) {
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[qq & (NSTAGE - 1)]);
   };
 
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+  for (int w = blockIdx.x; warp < NCW && w < n_items; w += gridDim.x) {
     const Item it = decode_item<2, UL_F32P>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
+    const uint32_t q0 = q;
     const int plane = vd.nz * vd.ny * vd.pitch;
+    const int np = it.pze - it.pzb + 1;
     const Ctx cx = column_ctx(it.x0 + tx, it.y0 + ty, vd);
-    float iqz;   // 1/Q of the column's centres on a z face
-    {
-      int cnt;
-      float Q;
-      box_counts(cx.X, cx.Y, 0, vd.nx, vd.ny, vd.nz, cnt, Q);
-      iqz = cnt > 0 ? __frcp_rn(Q) : 0.0f;
-    }
     if (tid == 0) {
       float lam[2], xi[2], cc[2][C];
 #pragma unroll
@@ -351,90 +366,96 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       for (int j = 0; j < C; ++j) s_ic.ncc[j] = make_float2(-cc[0][j], -cc[1][j]);
     }
     consumer_sync();
-    Fin3<C> fc;
-#pragma unroll
-    for (int j = 0; j < C; ++j) fc.ncc[j] = s_ic.ncc[j];
-    fc.nlam = s_ic.nlam;
-    fc.nxi = s_ic.nxi;
-    fc.floor = a.dist_floor;
-    const float iqc = cx.invQ_col;
-    const bool st = cx.col_ok;
-    float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
-    const int zstride = vd.ny * vd.pitch;
-
-    Slot3<C> s0, s1, s2, s3;
     Acc3<C> acc;
     acc.clear();
-    const int np = it.pze - it.pzb + 1;
-    const uint32_t q0 = q;
-    // the first step whose delayed finalisation is a centre of the item
-    const int kf = it.z0 - it.pzb + 2;
-    // the generic step covers the steps before the first interior-z centre
-    const int kh = kf + (it.z0 == 0 ? 1 : 0);
-    bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
-    // centre pzb (slot m of the first step) starts with no sums; centre
-    // pzb - 1 (slot l) is never finalised
-    s1.clear();
-    s2.clear();
-    if (ok) {
-      s2.x = xs_at(q0)[0];
-      s2.s = ss_at(q0)[0];
-      s2.e = s2.s < 0.0f ? 1.0f : 0.0f;
-    }
 
-    // One plane with slot values rotated afterwards (first and last planes
-    // of the item): the finalisation only from step kf on, the z-face 1/Q
-    // for centre 0, no wait past the item's last plane.
-    auto generic = [&](int kk) {
-      const uint32_t qq = q0 + kk;
-      const bool need2 = kk + 2 < np;
-      const bool landed2 = !need2 || mbar_test_wait(&full[(qq + 2) & (NSTAGE - 1)],
-                                                    ((qq + 2) / NSTAGE) & 1);
-      const int zd = it.pzb + kk - 2;
-      if (ok) {
-        const float invq = zd == 0 ? iqz : iqc;
-        float2* dst = col_dst + static_cast<long long>(zd) * zstride;
-        if (kk >= kf)
-          step3<C, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0, s1,
-                         s2, s3, invq, fc, acc, dst, plane, st);
-        else
-          step3<C, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
-                          s1, s2, s3, invq, fc, acc, dst, plane, st);
-      }
-      if (!landed2) ok = ok && wait_full(qq + 2);
-      if (kk >= 2) release(qq - 2);
-      s0 = s1;
-      s1 = s2;
-      s2 = s3;
-    };
-
-    int kk = 0;
-    for (; kk < kh && kk < np; ++kk) generic(kk);
-    // steady state: four planes per pass, slots in static rotation; every
-    // step has its finalisation, an interior-z centre, and two stages ahead
-    for (; ok && kk + 4 <= np - 2; kk += 4) {
-      const uint32_t qq = q0 + kk;
-      float2* dst = col_dst + static_cast<long long>(it.pzb + kk - 2) * zstride;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const uint32_t qr = qq + r;
-        const bool landed2 =
-            mbar_test_wait(&full[(qr + 2) & (NSTAGE - 1)], ((qr + 2) / NSTAGE) & 1);
-        Slot3<C>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
-        Slot3<C>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
-        Slot3<C>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
-        Slot3<C>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
-        step3<C, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l, m,
-                       h, iqc, fc, acc, dst + r * zstride, plane, st);
-        if (!landed2) ok = ok && wait_full(qr + 2);
-        release(qr - 2);
-      }
-    }
-    for (; kk < np; ++kk) generic(kk);
-
-    // After the last plane: s0 = centre pze - 1 (complete), s1 = centre pze
-    // (complete only when pze is the top plane of the volume).
     {
+      float iqz;   // 1/Q of the column's centres on a z face
+      {
+        int cnt;
+        float Q;
+        box_counts(cx.X, cx.Y, 0, vd.nx, vd.ny, vd.nz, cnt, Q);
+        iqz = cnt > 0 ? __frcp_rn(Q) : 0.0f;
+      }
+      Fin3<C> fc;
+#pragma unroll
+      for (int j = 0; j < C; ++j) fc.ncc[j] = s_ic.ncc[j];
+      fc.nlam = s_ic.nlam;
+      fc.nxi = s_ic.nxi;
+      fc.floor = a.dist_floor;
+      const float iqc = cx.invQ_col;
+      const bool st = cx.col_ok;
+      float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
+      const int zstride = vd.ny * vd.pitch;
+
+      Slot3<C> s0, s1, s2, s3;
+      // the first step whose delayed finalisation is a centre of the item
+      const int kf = it.z0 - it.pzb + 2;
+      // the generic step covers the steps before the first interior-z centre
+      const int kh = kf + (it.z0 == 0 ? 1 : 0);
+      bool ok = wait_full(q0) && (np < 2 || wait_full(q0 + 1));
+      // centre pzb (slot m of the first step) starts with no sums; centre
+      // pzb - 1 (slot l) is never finalised
+      s1.clear();
+      s2.clear();
+      if (ok) {
+        s2.x = xs_at(q0)[0];
+        s2.s = ss_at(q0)[0];
+        s2.xg = s2.s < 0.0f ? s2.x + 2.0f : s2.x;
+      }
+
+      // One plane with slot values rotated afterwards (first and last planes
+      // of the item): the finalisation only from step kf on, the z-face 1/Q
+      // for centre 0, no wait past the item's last plane.
+      auto generic = [&](int kk) {
+        const uint32_t qq = q0 + kk;
+        const bool need2 = kk + 2 < np;
+        const bool landed2 = !need2 || mbar_test_wait(&full[(qq + 2) & (NSTAGE - 1)],
+                                                      ((qq + 2) / NSTAGE) & 1);
+        const int zd = it.pzb + kk - 2;
+        if (ok) {
+          const float invq = zd == 0 ? iqz : iqc;
+          float2* dst = col_dst + static_cast<long long>(zd) * zstride;
+          if (kk >= kf)
+            step3<C, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
+                           s1, s2, s3, invq, fc, acc, dst, plane, st);
+          else
+            step3<C, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6),
+                            s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
+        }
+        if (!landed2) ok = ok && wait_full(qq + 2);
+        if (kk >= 2) release(qq - 2);
+        s0 = s1;
+        s1 = s2;
+        s2 = s3;
+      };
+
+      int kk = 0;
+      for (; kk < kh && kk < np; ++kk) generic(kk);
+      // steady state: four planes per pass, slots in static rotation; every
+      // step has its finalisation, an interior-z centre, and two stages ahead
+      for (; ok && kk + 4 <= np - 2; kk += 4) {
+        const uint32_t qq = q0 + kk;
+        float2* dst = col_dst + static_cast<long long>(it.pzb + kk - 2) * zstride;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t qr = qq + r;
+          const bool landed2 =
+              mbar_test_wait(&full[(qr + 2) & (NSTAGE - 1)], ((qr + 2) / NSTAGE) & 1);
+          Slot3<C>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
+          Slot3<C>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
+          Slot3<C>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
+          Slot3<C>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
+          step3<C, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l,
+                         m, h, iqc, fc, acc, dst + r * zstride, plane, st);
+          if (!landed2) ok = ok && wait_full(qr + 2);
+          release(qr - 2);
+        }
+      }
+      for (; kk < np; ++kk) generic(kk);
+
+      // After the last plane: s0 = centre pze - 1 (complete), s1 = centre pze
+      // (complete only when pze is the top plane of the volume).
       const uint32_t ql = q0 + np - 1;
       const bool live = ok && !*reinterpret_cast<volatile int*>(&s_abort);
       const int zl = it.pze - 1;
@@ -496,6 +517,15 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       }
     }
     consumer_sync();
+  }
+
+  // After a timeout the consumers skipped their waits: before the CTA exits,
+  // wait (bounded) for the copies still landing in its shared memory.  No
+  // load is issued after the abort, so each stage has at most one.
+  __syncthreads();
+  if (tid == 0 && *reinterpret_cast<volatile int*>(&s_abort)) {
+    for (int s = 0; s < NSTAGE; ++s)
+      if (lastq[s] != 0xffffffffu) mbar_wait_bounded(&full[s], (lastq[s] / NSTAGE) & 1);
   }
 }
 

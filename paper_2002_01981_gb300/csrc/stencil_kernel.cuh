@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   extern __shared__ unsigned char dsmem_raw[];
   __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ __align__(8) uint64_t empty[NSTAGE];
+  __shared__ int lastq[NSTAGE];         // the last plane loaded into each stage
   __shared__ ItemTable tab;
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
@@ -646,6 +647,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       (reinterpret_cast<uintptr_t>(dsmem_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   // Active units of every volume, compacted one volume per warp (ballots).
   constexpr bool kPairUnits = paired(UL) && NP == 2;
@@ -675,6 +677,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCW);
+      lastq[s] = -1;
     }
     fence_mbarrier_init();
   }
@@ -700,10 +703,12 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   };
 
   // ------------------------------------------------------------ producer
+  // (after a timeout it stops loading and joins the CTA's final drain)
   if (warp == NCW) {
     if (lane == 0) {
       int q = 0;
-      for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+      bool go = true;
+      for (int w = blockIdx.x; go && w < n_items; w += gridDim.x) {
         const Item it = decode_item<NP, UL>(a, tab, w);
         const VolDesc& vd = a.vol[it.v];
         const CUtensorMap* mx = &a.tm_x[it.v];
@@ -711,12 +716,18 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
           const int s = q % NSTAGE;
           if (q >= NSTAGE &&
-              !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((q / NSTAGE) - 1) & 1))) {
+              !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((q / NSTAGE) - 1) & 1),
+                                 wait_ns)) {
             atomicExch(&s_abort, 1);
             set_status(a.status, IFCM_ERR_TIMEOUT, 3);
-            return;
+            go = false;
+            break;
           }
-          if (*reinterpret_cast<volatile int*>(&s_abort)) return;
+          if (*reinterpret_cast<volatile int*>(&s_abort)) {
+            go = false;
+            break;
+          }
+          lastq[s] = q;
           // a plane of the tile's column, or in 2D the tile of step pz
           const int ty0 = FLAT ? pz * TY : it.y0;
           const int tz0 = FLAT ? 0 : pz;
@@ -730,8 +741,7 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
         }
       }
     }
-    return;
-  }
+  } else {
 
   // ------------------------------------------------------------ consumers
   const int tx = tid & 31, ty = tid >> 5;
@@ -747,7 +757,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   // so that all consumer threads still reach the same barriers).
   auto wait_full = [&](int qq) -> bool {
     if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
-    if (!mbar_wait_bounded(&full[qq % NSTAGE], static_cast<uint32_t>((qq / NSTAGE) & 1))) {
+    if (!mbar_wait_bounded(&full[qq % NSTAGE], static_cast<uint32_t>((qq / NSTAGE) & 1),
+                           wait_ns)) {
       atomicExch(&s_abort, 1);
       set_status(a.status, IFCM_ERR_TIMEOUT, 4);
       return false;
@@ -987,6 +998,16 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       }
     }
     consumer_sync();
+  }
+  }   // consumers
+
+  // After a timeout the consumers skipped their waits: before the CTA exits,
+  // wait (bounded) for the copies still landing in its shared memory.  The
+  // producer issues no load after the abort, so each stage has at most one.
+  __syncthreads();
+  if (tid == 0 && *reinterpret_cast<volatile int*>(&s_abort)) {
+    for (int s = 0; s < NSTAGE; ++s)
+      if (lastq[s] >= 0) mbar_wait_bounded(&full[s], static_cast<uint32_t>((lastq[s] / NSTAGE) & 1));
   }
 }
 // ---------------------------------------------------------------------------

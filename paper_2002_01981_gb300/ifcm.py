@@ -541,7 +541,13 @@ def profile_enable(on=True):
     N.load().ifcm_profile_enable(1 if on else 0)
 
 
-PROF_STENCIL, PROF_ADJOINT_POINT, PROF_ADJOINT_GATHER = 0, 1, 2
+PROF_STENCIL, PROF_ADJOINT_POINT, PROF_ADJOINT_GATHER, PROF_STENCIL3D = 0, 1, 2, 3
+
+
+def set_wait_limit_ns(ns=0):
+    """Bound (ns) of every wait of the kernels on their shared-memory tiles;
+    0 restores the default (about one second).  See ifcm_set_wait_limit_ns."""
+    N.load().ifcm_set_wait_limit_ns(int(ns))
 
 
 def profile_read(kind=PROF_STENCIL):
