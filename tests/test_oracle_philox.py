@@ -45,6 +45,18 @@ def test_uniform53_extremes_and_range():
     assert abs(u.mean() - 0.5) < 5 * (1 / np.sqrt(12 * 1000))
 
 
+def test_uniform53_takes_the_high_bits_of_r0_then_r1():
+    # double = ((r0 >> 5) * 2^26 + (r1 >> 6)) * 2^-53: r0 gives the top 27 bits
+    w = lambda r0, r1: np.array([r0, r1], dtype=np.uint64)
+    assert philox.uniform53(w(0x80000000, 0)) == 0.5
+    assert philox.uniform53(w(0, 0x80000000)) == 2.0 ** -28
+    assert philox.uniform53(w(0xFFFFFFFF, 0)) == (2.0 ** 27 - 1) * 2.0 ** -27
+    assert philox.uniform53(w(0, 0xFFFFFFFF)) == (2.0 ** 26 - 1) * 2.0 ** -53
+    assert philox.uniform53(w(0x00000020, 0x00000040)) == 2.0 ** -27 + 2.0 ** -53
+    # the bits dropped by the shifts do not count
+    assert philox.uniform53(w(0x1F, 0x3F)) == 0.0
+
+
 def test_streams_are_distinct():
     a = philox.swarm_uniform(1, 0, np.arange(8), 0, philox.STREAM_P1)
     b = philox.swarm_uniform(1, 0, np.arange(8), 0, philox.STREAM_P2)

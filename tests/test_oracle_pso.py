@@ -119,3 +119,42 @@ def test_onestep_fitness_carries_each_particle_state():
         for p in range(2):
             J = ifcm.ifcm_fit(x, U0, C0, lam_xi[p, 0], lam_xi[p, 1], 2.0, g + 1, 0.0)[2]
             assert f[p] == J
+
+
+def test_one_step_computed_by_hand(monkeypatch):
+    # Alg 1 steps 5-8 on three particles with given draws p1, p2 (stream 2 and
+    # 3 of the generator), every value worked out by hand:
+    # step 5: particle 1 improves (0.5 < 1.0) and takes its position as pbest;
+    #         particles 0 (4.0 > 3.0) and 2 (2.5 > 2.0) keep theirs;
+    # step 6: every ring of three holds all three, so lbest = particle 1,
+    #         lbest_x = (0.60, 0.40);
+    # step 7: v <- v + p1 (pbest_x - x) + p2 (lbest_x - x), clamped to +-0.2;
+    # step 8: x <- clip(x + v, 0, 1).
+    p1 = np.array([[0.25, 0.5], [0.75, 0.125], [0.5, 0.375]])
+    p2 = np.array([[0.5, 0.25], [0.375, 0.625], [0.125, 0.75]])
+
+    def draws(seed, gen, i, d, stream):
+        assert stream in (pso.STREAM_P1, pso.STREAM_P2)
+        return np.broadcast_to(p1 if stream == pso.STREAM_P1 else p2, (3, 2)).copy()
+
+    s = pso.Swarm(3, seed=1)
+    s.x = np.array([[0.50, 0.50], [0.60, 0.40], [0.90, 0.10]])
+    s.v = np.array([[0.01, -0.02], [0.05, 0.0], [-0.03, 0.04]])
+    s.pbest_x = np.array([[0.55, 0.45], [0.70, 0.30], [0.85, 0.20]])
+    s.pbest_f = np.array([3.0, 1.0, 2.0])
+    monkeypatch.setattr(pso, "swarm_uniform", draws)
+    pso.pso_step(s, np.array([4.0, 0.5, 2.5]))
+    # particle 0: pbest - x = (0.05, -0.05), lbest - x = (0.10, -0.10)
+    #   v = (0.01 + 0.25*0.05 + 0.5*0.10, -0.02 + 0.5*(-0.05) + 0.25*(-0.10))
+    #     = (0.0725, -0.07); x = (0.5725, 0.43)
+    # particle 1: both differences are 0: v = (0.05, 0.0); x = (0.65, 0.40)
+    # particle 2: pbest - x = (-0.05, 0.10), lbest - x = (-0.30, 0.30)
+    #   v = (-0.03 - 0.025 - 0.0375, 0.04 + 0.0375 + 0.225) = (-0.0925, 0.3025)
+    #   -> clamped (-0.0925, 0.2); x = (0.8075, 0.30)
+    v_hand = np.array([[0.0725, -0.07], [0.05, 0.0], [-0.0925, 0.2]])
+    x_hand = np.array([[0.5725, 0.43], [0.65, 0.40], [0.8075, 0.30]])
+    assert np.allclose(s.v, v_hand, rtol=0, atol=1e-15)
+    assert np.allclose(s.x, x_hand, rtol=0, atol=1e-15)
+    assert np.array_equal(s.pbest_f, [3.0, 0.5, 2.0])
+    assert np.allclose(s.pbest_x, [[0.55, 0.45], [0.60, 0.40], [0.85, 0.20]], rtol=0, atol=0)
+    assert s.gen == 1
