@@ -841,6 +841,26 @@ def run_ours(args):
     return 0
 
 
+def relaunch(n):
+    """--gpus N under a plain interpreter: start the N ranks (one process per
+    GPU) through torch.distributed.run with the same arguments, or stop with
+    an error when fewer than N GPUs are visible."""
+    import socket
+
+    import torch
+    have = torch.cuda.device_count() if torch.cuda.is_available() else 0
+    if have < n:
+        print(f"bench.py: --gpus {n} asks for {n} GPUs but {have} are visible", file=sys.stderr)
+        return 2
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -864,6 +884,8 @@ def main():
     ap.add_argument("--small-kind", choices=("bf16", "grad"), default=None,
                     help="profiling case of the bf16 stencil or of the adjoint kernels")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return relaunch(args.gpus)
     if args.impl == "reference":
         return run_reference(args)
     if args.small_kind:

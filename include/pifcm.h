@@ -20,9 +20,11 @@
  * - Memberships are float32 arrays [c][nz][ny][pitch_x] (one plane per
  *   cluster); padding elements of outputs are unspecified.
  * - "device" pointers are CUDA device memory owned by the caller; "host"
- *   pointers are ordinary host memory owned by the caller.  The library never
- *   allocates: its only scratch is the caller's workspace `ws` of at least the
+ *   pointers are ordinary host memory owned by the caller.  The library does
+ *   not allocate: its scratch is the caller's workspace `ws` of at least the
  *   size the matching *_workspace_bytes() call returns (256-byte aligned).
+ *   The one exception is ifcm_fit_noalloc, whose scratch is a static 64 MiB
+ *   device array of the library (see there).
  * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *   stream-ordered and return without synchronising, except the *_host entry
  *   points, which synchronise the stream before returning.
@@ -376,19 +378,31 @@ ifcm_status ifcm_polish(const float* x, ifcm_shape shape, const ifcm_params* p, 
  * plugin whose host framework owns every allocation and hands it only its
  * input and output pointers, a loop that must not take the allocator's
  * implicit synchronisation).  Arguments and results are those of ifcm_fit;
- * the scratch is a 64 MiB array held by the library on every GPU that loads
- * it, until the process exits.  Calls whose ifcm_fit workspace would exceed
- * 64 MiB (about 1.36 million voxels at c = 4, e.g. 111^3) return IFCM_ERR_NOMEM with a
- * message naming both sizes.  The first call on each device looks up the
- * array's device address; make that first call before any stream capture.
- * Every call on a device shares the one array: calls that overlap on the GPU
- * (other streams, other threads) race and corrupt each other's results, so
- * serialise them.  No call allocates or frees device memory.
+ * the scratch is a static 64 MiB device array of the library.  The CUDA
+ * runtime places it in a GPU's memory when it loads the library's module on
+ * that GPU -- with lazy module loading (the default), at the first call of
+ * this entry point there -- and it stays until the process exits; that first
+ * call can therefore fail with IFCM_ERR_CUDA when the GPU has no room for it.
+ * Calls whose ifcm_fit workspace would exceed 64 MiB (about 1.36 million
+ * voxels at c = 4, e.g. 111^3) return IFCM_ERR_NOMEM with a message naming
+ * both sizes.  The first call on each device looks up the array's device
+ * address and keeps it for the process (a cudaDeviceReset makes it stale);
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and corrupt each other's results, so serialise them.  The
+ * entry point calls no allocating routine; device-side failures of a call
+ * (a bounded wait that ran out) go to the status word in the array, which
+ * ifcm_fit_noalloc_status reports.
  */
 ifcm_status ifcm_fit_noalloc(const float* x, ifcm_shape shape, const ifcm_params* p,
                              const double* lam_xi, const float* u_init, const double* c_init,
                              float* u_out, double* c_out, double* J_out, int32_t* iters_out,
                              void* stream);
+/* The device status of the last ifcm_fit_noalloc call on the current device,
+ * as ifcm_device_status reports it for a workspace: synchronises `stream`,
+ * returns IFCM_OK or the condition the kernels recorded (IFCM_ERR_TIMEOUT for
+ * a bounded wait that ran out).  The paper has no counterpart. */
+ifcm_status ifcm_fit_noalloc_status(void* stream);
 
 /* ---------------------------------------------------------------------------
  * Profiling counters (host side, per process): when enabled, the library

@@ -16,6 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libpifcm.so")
+# The checked build: every computed global index of the kernels is tested
+# against its buffer's extent (IFCM_ERR_BOUNDS on a violation, no trap).
+CHECKED_BUILD_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB_PATH = os.path.join(HERE, "libpifcm_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -39,23 +43,28 @@ def _inputs():
             [os.path.abspath(__file__)])
 
 
-def up_to_date():
-    if not os.path.exists(LIB_PATH):
+def up_to_date(lib=LIB_PATH):
+    if not os.path.exists(lib):
         return False
-    lib_t = os.path.getmtime(LIB_PATH)
+    lib_t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= lib_t for p in _inputs())
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link libpifcm.so; returns its path."""
-    if not force and up_to_date():
-        return LIB_PATH
+def build(force=False, verbose=False, extra_flags=(), checked=False):
+    """Compile and link libpifcm.so (or, with checked, libpifcm_checked.so
+    built with -DIFCM_CHECKED); returns its path."""
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
+    build_dir = CHECKED_BUILD_DIR if checked else BUILD_DIR
+    if checked:
+        extra_flags = ("-DIFCM_CHECKED", *extra_flags)
+    if not force and up_to_date(lib_path):
+        return lib_path
     nvcc = nvcc_path()
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", INCLUDE, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -71,15 +80,15 @@ def build(force=False, verbose=False, extra_flags=()):
             print(text, file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     link = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
     if verbose:
         print(" ".join(link), flush=True)
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -11,6 +11,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 
 using namespace pifcm;
@@ -188,6 +190,8 @@ struct RunBufs {
   int rec_per_particle[kMaxVols];
   double* partials;
   float* dmax;
+  long long n_records;          // records carved (all volumes)
+  long long buf_elems[kMaxVols];   // 4-byte elements of each ua / ub buffer
   RunState st;
 };
 
@@ -211,6 +215,7 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
   int pb = 0;
   for (int v = 0; v < n; ++v) {
     const size_t pl = plane_elems(shapes[v]);
+    r.buf_elems[v] = static_cast<long long>(run_buffer_elems(c, P[v], layout) * pl);
     r.ua[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
     r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
     r.u0p[v] = layout == UL_PLANAR ? nullptr
@@ -226,6 +231,7 @@ RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, in
     recs += static_cast<long long>(P[v]) * nrec;
     pb += P[v];
   }
+  r.n_records = recs;
   r.partials = cv.take<double>(static_cast<size_t>(recs) * (2 * c + 1));
   r.dmax = cv.take<float>(static_cast<size_t>(recs));
   r.st.centres = cv.take<double>(static_cast<size_t>(pb) * c);
@@ -380,6 +386,23 @@ cudaEvent_t prof_begin(cudaStream_t s, cudaEvent_t* end_out, int kind = IFCM_PRO
   return ev.first;
 }
 
+// ------------------------------------------------------------ tracing
+// NVTX ranges on the host thread around the enqueueing of a run's phases
+// (the run, the FCM start, each generation, each IFCM iteration, the final
+// run).  They cost a few instructions when no tool is attached; a profiler
+// that records NVTX (e.g. Nsight Systems) shows them beside the launches.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  Trace(const char* fmt, int i) {
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), fmt, i);
+    nvtxRangePushA(buf);
+  }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
+
 // ------------------------------------------------------------ run loops
 void fill_method(StencilArgs& a, const ifcm_params* p) {
   a.dist_floor = static_cast<float>(p->dist_floor);
@@ -489,6 +512,7 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
   a.active = rb.st.active;
   a.partials = rb.partials;
   a.dmax = rb.dmax;
+  a.n_records = rb.n_records;
   a.status = status;
   a.sum_one = kind != 0;   // later iterations read Eq 2's memberships
   a.wait_ns = g_wait_ns.load();
@@ -512,6 +536,8 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.rec_base = rb.rec_base[v];
     d.lam_xi = bv.lam_xi;
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
+    d.dst_elems = rb.buf_elems[v];
+    d.status = status;
     const bool k3 = stencil3d_eligible(rb.layout, pl.np, a.m_is_2, a.sum_one, s.nz);
     ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0, 4, !k3));
     ST_TRY(make_smap(&a.tm_s[v], rb.gs[v], s));
@@ -525,12 +551,14 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
       d.u_src = src;
       d.src_pstride = kind == 0 ? 0 : static_cast<long long>(K) * plane;   // in words
       d.src_cstride = kind == 0 ? 0 : K;
+      d.src_planes = kind == 0 ? K : units * K;
       ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? K : units * K, K, wb));
     } else {
       const float* src = kind == 0 ? bv.u0 : (kind == 1 ? rb.ua[v] : rb.ub[v]);
       d.u_src = src;
       d.src_pstride = kind == 0 ? 0 : static_cast<long long>(c) * plane;
       d.src_cstride = kind == 0 ? 0 : c;
+      d.src_planes = kind == 0 ? c : bv.P * c;
       ST_TRY(make_map(&a.tm_u[v], src, s, kind == 0 ? c : bv.P * c, c));
     }
   }
@@ -690,6 +718,7 @@ struct BatchRun {
     r.P_total = P_total;
     r.partials = rb->partials;
     r.dmax = rb->dmax;
+    r.n_records = rb->n_records;
     r.st = rb->st;
     r.max_iter = max_iter;
     r.eps = eps;
@@ -711,6 +740,7 @@ struct BatchRun {
   }
 
   ifcm_status iteration(int it, cudaStream_t st) {
+    const Trace tr("ifcm iteration %d", it);
     const int c = p->c;
     const int kind = it == 0 ? 0 : (it % 2 == 1 ? 1 : 2);
     if (!wide) {
@@ -747,6 +777,8 @@ struct BatchRun {
         a.active = rb->st.active + rb->pbase[v];
         a.partials = rb->partials + static_cast<size_t>(rb->rec_base[v]) * (2 * c + 1);
         a.dmax = rb->dmax + rb->rec_base[v];
+        a.n_records = rb->n_records - rb->rec_base[v];
+        a.dst_elems = rb->buf_elems[v];
         a.stencil = 1;
         sh.P = bv.P;
         sh.n_rec = blocks;
@@ -829,6 +861,8 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   a.active = rb.st.active;
   a.partials = rb.partials;
   a.dmax = rb.dmax;
+  a.n_records = rb.n_records;
+  a.dst_elems = rb.buf_elems[0];
   ShellArgs sh;
   fill_plain_method(a, sh, p);
   sh.n_rec = blocks;
@@ -839,6 +873,7 @@ ifcm_status run_plain(const float* x, const ifcm_shape& s, const ifcm_params* p,
   r.P_total = 1;
   r.partials = rb.partials;
   r.dmax = rb.dmax;
+  r.n_records = rb.n_records;
   r.st = rb.st;
   r.max_iter = max_iter;
   r.eps = p->eps_u;
@@ -1415,6 +1450,7 @@ size_t pifcm3d_workspace_bytes(ifcm_shape shape, const ifcm_params* p, const pif
 ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
                     const pifcm_options* o, float* u_out, pifcm_result* result, void* ws,
                     size_t ws_bytes, void* stream) {
+  const Trace trace_run("pifcm3d");
   ST_TRY(check_shape(shape));
   ST_TRY(check_params(p));
   ST_TRY(check_extent(shape, p));
@@ -1445,8 +1481,11 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   RunBufs rb = b.run;
   rb.st.updates = b.updates;
   // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c.
-  ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter, rb,
-                   b.iters_init, b.c0, b.J_init, b.status, false, st));
+  {
+    const Trace tr("fcm start");
+    ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter,
+                     rb, b.iters_init, b.c0, b.J_init, b.status, false, st));
+  }
   CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0,
                             static_cast<long long>(c) * rpl, st));
 
@@ -1468,17 +1507,20 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
     BatchRun br;
     ST_TRY(br.prepare(&bv, 1, p, rb, b.status, o->generations, 0.0, st));
     for (int g = 0; g < o->generations; ++g) {
+      const Trace tr("generation %d", g);
       ST_TRY(br.iteration(g, st));
       CU_TRY(launch_pso_step(sw, b.fitness, st));
     }
   } else {
     for (int g = 0; g < o->generations; ++g) {
+      const Trace tr("generation %d", g);
       ST_TRY(run_stencil(xr, rs, p, sw.x, P, b.u0, b.c0, rb, b.fitness, b.iters, nullptr,
                          b.status, st));
       CU_TRY(launch_pso_step(sw, b.fitness, st));
     }
   }
   // Algorithm 1 step 11: final IFCM at the best personal best.
+  const Trace tr("final run");
   CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));
   ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
                      b.c_final, b.status, st));
@@ -1647,6 +1689,7 @@ ifcm_status grad_forward(const float* x, const ifcm_shape& s, const ifcm_params*
   r.P_total = 1;
   r.partials = rb.partials;
   r.dmax = rb.dmax;
+  r.n_records = rb.n_records;
   r.st = rb.st;
   r.max_iter = K;
   r.eps = 0.0;

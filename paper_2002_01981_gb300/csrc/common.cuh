@@ -27,6 +27,20 @@ __device__ __forceinline__ void set_status(DevStatus* s, int code, int where) {
   if (atomicCAS(&s->status, 0, code) == 0) s->where = where;
 }
 
+// The checked build (-DIFCM_CHECKED): every computed global index of the
+// kernels is tested against the extent of its buffer before the access; a
+// violation records IFCM_ERR_BOUNDS with the site in the status word and the
+// access is skipped (no trap).  In the normal build the test is `true`.
+#ifdef IFCM_CHECKED
+__device__ __forceinline__ bool check_index(bool ok, DevStatus* s, int where) {
+  if (!ok) set_status(s, IFCM_ERR_BOUNDS, where);
+  return ok;
+}
+#define IFCM_CHECK(cond, st, where) ::pifcm::check_index((cond), (st), (where))
+#else
+#define IFCM_CHECK(cond, st, where) true
+#endif
+
 // ---------------------------------------------------------------- PTX glue
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

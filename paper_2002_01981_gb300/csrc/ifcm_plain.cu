@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(PT) plain_shell_kernel(const PlainArgs a, cons
     voxel_update<C>(H, F, xc, cc, k, u, um, Jv);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      a.u_dst[doff + j * plane + off] = u[j];
+      if (IFCM_CHECK(doff + static_cast<long long>((j + 1) * plane) <= a.dst_elems, a.status, 41))
+        a.u_dst[doff + j * plane + off] = u[j];
       s0[j] += um[j];
       s1[j] = fmaf(um[j], xc, s1[j]);
       dm = fmaxf(dm, fabsf(u[j] - uc[j]));
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(PT) plain_shell_kernel(const PlainArgs a, cons
   }
   __syncthreads();
   const size_t rec = static_cast<size_t>(pid) * sh.n_rec + blockIdx.x;
-  if (threadIdx.x < 2 * C + 1) {
+  if (!IFCM_CHECK(static_cast<long long>(rec) < a.n_records, a.status, 42)) {
+  } else if (threadIdx.x < 2 * C + 1) {
     double sum = 0.0;
 #pragma unroll
     for (int w = 0; w < PT / 32; ++w) sum += static_cast<double>(s_red[w][threadIdx.x]);
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
   float mx = 0.0f;
   const long long first = rv.rec_base + static_cast<long long>(p) * rv.n_rec;
+  if (!IFCM_CHECK(first >= 0 && first + rv.n_rec <= a.n_records, a.status, 40)) return;
   const double* rec = a.partials + first * NV;
   if (a.reduce == IFCM_REDUCE_COMP32) {
     float(*fs)[RT] = reinterpret_cast<float(*)[RT]>(&s_sum[0][0]);

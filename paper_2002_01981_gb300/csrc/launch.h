@@ -37,6 +37,9 @@ struct VolDesc {
   const float* u_src;           // particle 0's U^t (for the rare flat-neighbourhood path)
   long long src_pstride;        // elements between particles' U^t (0: one shared U^t)
   int src_cstride;              // TMA cluster-coordinate step per particle (c or 0)
+  int src_planes;               // planes of the U^t tensor map (checked build)
+  long long dst_elems;          // 4-byte elements of the U^{t+1} buffer (checked build)
+  DevStatus* status;            // the launch's status word (checked build)
 };
 
 // Kernel parameter block (passed as __grid_constant__, so the tensor maps
@@ -51,6 +54,7 @@ struct StencilArgs {
   const int32_t* active;        // [particles of the launch]
   double* partials;             // [records][2c+1]
   float* dmax;                  // [records]
+  long long n_records;          // records of the workspace (checked build)
   float dist_floor, m, inv_m1;
   int m_is_2;
   int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across warps
@@ -97,6 +101,8 @@ struct PlainArgs {
   const int32_t* active;        // [P]
   double* partials;             // [P][n_rec][2c+1]
   float* dmax;                  // [P][n_rec]
+  long long n_records;          // records from partials on (checked build)
+  long long dst_elems;          // elements of u_dst (checked build)
   float dist_floor, m, inv_m1;
   int m_is_2;
   int vpt;                      // voxels per thread
@@ -140,6 +146,7 @@ struct ReduceArgs {
   int P_total;                  // particles of the launch (one CTA each)
   const double* partials;       // [records][2c+1]
   const float* dmax;            // [records]
+  long long n_records;          // records of the workspace (checked build)
   RunState st;                  // arrays over the launch's particles
   int max_iter;
   double eps;

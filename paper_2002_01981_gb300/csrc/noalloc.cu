@@ -6,8 +6,10 @@
 // only the device pointers of their inputs and outputs and owns every other
 // allocation, or latency-bound loops that must not take the allocator's
 // implicit synchronisation.  ifcm_fit asks them for a workspace; this entry
-// point needs none.  Its scratch is the fixed device array below, which every
-// GPU that loads the library holds until the process exits.
+// point needs none.  Its scratch is the fixed device array below.  The CUDA
+// runtime places it in a GPU's memory when it loads this library's module on
+// that GPU -- with lazy module loading, at the first call there -- and it
+// stays until the process exits.
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -84,4 +86,13 @@ extern "C" ifcm_status ifcm_fit_noalloc(const float* x, ifcm_shape shape, const 
   // earlier call are harmless.
   return ifcm_fit(x, shape, p, lam_xi, u_init, c_init, u_out, c_out, J_out, iters_out, scratch,
                   kNoAllocScratchBytes, stream);
+}
+
+// The device status word of the last ifcm_fit_noalloc call on the current
+// device (it sits at the start of the static scratch, as in any workspace).
+extern "C" ifcm_status ifcm_fit_noalloc_status(void* stream) {
+  void* scratch = nullptr;
+  const ifcm_status s = scratch_on_current_device(&scratch);
+  if (s != IFCM_OK) return s;
+  return ifcm_device_status(scratch, stream);
 }

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     voxel_update<C>(H, F, xc, cc, k, u, um, Jv);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      a.u_dst[j * plane + off] = u[j];
+      if (IFCM_CHECK(static_cast<long long>((j + 1) * plane) <= a.dst_elems, a.status, 43))
+        a.u_dst[j * plane + off] = u[j];
       s0[j] += um[j];
       s1[j] = fmaf(um[j], xc, s1[j]);
       dm = fmaxf(dm, fabsf(u[j] - uc[j]));
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(PT) plain_kernel(const PlainArgs a) {
     s_red[warp][2 * C + 1] = vm;
   }
   __syncthreads();
-  if (threadIdx.x < 2 * C + 1) {
+  if (!IFCM_CHECK(static_cast<long long>(blockIdx.x) < a.n_records, a.status, 44)) {
+  } else if (threadIdx.x < 2 * C + 1) {
     double sum = 0.0;
 #pragma unroll
     for (int w = 0; w < PT / 32; ++w) sum += static_cast<double>(s_red[w][threadIdx.x]);

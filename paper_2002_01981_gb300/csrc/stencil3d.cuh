@@ -66,6 +66,11 @@ __host__ __device__ constexpr int s3_smem_total() {
 }
 static_assert(NSTAGE == 8, "stage indices are taken modulo 8 with a mask");
 static_assert(SBYTES % 128 == 0, "TMA destinations start on 128-byte boundaries");
+// every shared-memory read of a column stays inside its stage plane: the
+// column's centre (ty + 1) BX + tx + 4 plus neighbour offsets of -BX - 1 ...
+// BX + 1, for tx < TX and ty < TY
+static_assert(BX + 4 - BX - 1 >= 0 && TY * BX + TX - 1 + 4 + BX + 1 < PLANE,
+              "stencil reads stay inside the stage plane");
 
 // One centre of the column: its sums over the planes read so far.
 template <int C>
@@ -239,7 +244,9 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       const bool on = p < units && (a.active[vd.pbase + 2 * p] != 0 ||
                                     (2 * p + 1 < vd.P && a.active[vd.pbase + 2 * p + 1] != 0));
       const unsigned msk = __ballot_sync(0xffffffffu, on);
-      if (on) tab.act[vd.pbase + n + __popc(msk & ((1u << lane) - 1u))] = static_cast<short>(p);
+      const int ia = vd.pbase + n + __popc(msk & ((1u << lane) - 1u));
+      if (on && IFCM_CHECK(ia >= 0 && ia < kMaxBatchParticles, a.status, 30))
+        tab.act[ia] = static_cast<short>(p);
       n += __popc(msk);
     }
     if (lane == 0) {
@@ -273,6 +280,9 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   auto load_plane = [&](uint32_t qq, const Item& it, int pz) {
     const VolDesc& vd = a.vol[it.v];
     const uint32_t s = qq & (NSTAGE - 1);
+    if (!IFCM_CHECK(pz >= 0 && pz < vd.nz && it.unit * vd.src_cstride + C <= vd.src_planes,
+                    a.status, 31))
+      return;
     unsigned char* st = dsmem + s * SB;
     lastq[s] = qq;
     mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C>());
@@ -384,7 +394,12 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       fc.nxi = s_ic.nxi;
       fc.floor = a.dist_floor;
       const float iqc = cx.invQ_col;
-      const bool st = cx.col_ok;
+      // stores of the column (the item's centres lie in [z0, z1) of the volume)
+      const bool st = cx.col_ok &&
+                      IFCM_CHECK(it.z0 >= 0 && it.z1 <= vd.nz &&
+                                     (static_cast<long long>(it.unit) + 1) * C * plane * 2 <=
+                                         vd.dst_elems,
+                                 a.status, 32);
       float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
       const int zstride = vd.ny * vd.pitch;
 
@@ -496,7 +511,8 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       if (p == 0 ? it.on0 : it.two) {
         const int pid = p == 0 ? it.p0 : it.p1;
         const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
-        if (v < 2 * C + 1) {
+        if (!IFCM_CHECK(rec >= 0 && rec < a.n_records, a.status, 33)) {
+        } else if (v < 2 * C + 1) {
           if (a.reduce == IFCM_REDUCE_FP64) {
             double sum = 0.0;
 #pragma unroll

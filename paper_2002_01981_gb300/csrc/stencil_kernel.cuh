@@ -478,7 +478,14 @@ __device__ __forceinline__ void finalize_centre(const Slot<C, NP>& sl, const flo
                                                 const MethodConsts& k, Sums<C, NP>& acc,
                                                 bool live = true) {
   constexpr int K = Pairs<C, NP>::K;
-  const bool keep = !MASK || live;
+  // the stores of this centre: its plane and its unit's (or particle's)
+  // U^{t+1} planes inside the destination buffer
+  const long long plane_l = static_cast<long long>(a.nz) * a.ny * a.pitch;
+  const long long unit_end =
+      paired(UL) ? (static_cast<long long>(it.unit) + 1) * K * plane_l * (word_bytes(UL) / 4)
+                 : (static_cast<long long>(it.two ? max(it.p0, it.p1) : it.p0) + 1) * C * plane_l;
+  const bool keep = (!MASK || live) &&
+                    IFCM_CHECK(z >= 0 && z < a.nz && unit_end <= a.dst_elems, a.status, 22);
   if (MASK) xc = keep ? xc : 0.0f;    // x is NaN outside the volume
   float2 H[K], F[K];
   if (FAST) {
@@ -664,7 +671,9 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       else
         on = p < units && a.active[vd.pbase + p] != 0;
       const unsigned m = __ballot_sync(0xffffffffu, on);
-      if (on) tab.act[vd.pbase + n + __popc(m & ((1u << lane) - 1u))] = static_cast<short>(p);
+      const int ia = vd.pbase + n + __popc(m & ((1u << lane) - 1u));
+      if (on && IFCM_CHECK(ia >= 0 && ia < kMaxBatchParticles, a.status, 20))
+        tab.act[ia] = static_cast<short>(p);
       n += __popc(m);
     }
     if (lane == 0) {
@@ -726,6 +735,18 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
           if (*reinterpret_cast<volatile int*>(&s_abort)) {
             go = false;
             break;
+          }
+          {
+            const int unit = paired(UL) ? it.unit : it.p0;
+            const int K = paired(UL) ? Pairs<C, NP>::K : C;
+            const int last = (NP == 2 && !paired(UL)) ? it.p1 : unit;
+            const int ext = FLAT ? (vd.ny + TY - 1) / TY : vd.nz;
+            if (!IFCM_CHECK(pz >= 0 && pz < ext && unit * vd.src_cstride + K <= vd.src_planes &&
+                                last * vd.src_cstride + K <= vd.src_planes,
+                            a.status, 21)) {
+              go = false;
+              break;
+            }
           }
           lastq[s] = q;
           // a plane of the tile's column, or in 2D the tile of step pz
@@ -977,7 +998,8 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
       if (p == 0 ? it.on0 : it.two) {
         const int pid = p == 0 ? it.p0 : it.p1;
         const long long rec = vd.rec_base + static_cast<long long>(pid) * vd.n_tiles + it.tile;
-        if (v < 2 * C + 1) {
+        if (!IFCM_CHECK(rec >= 0 && rec < a.n_records, a.status, 23)) {
+        } else if (v < 2 * C + 1) {
           if (a.reduce == IFCM_REDUCE_FP64) {
             double sum = 0.0;
 #pragma unroll
