@@ -82,12 +82,13 @@ ifcm_status check_params(const ifcm_params* p) {
 bool is_bf16(const ifcm_params* p) { return p->u_dtype == IFCM_U_BF16; }
 
 // Layout of the memberships between iterations for a batch of P_total
-// particles: bf16 pair words when asked for; FP32 planes for one-particle runs
-// (their workspace stays c planes per buffer) and for V > 1 shells (the plain
-// kernel); float2 pair words for every other FP32 batch.
+// particles: bf16 pair words when asked for; FP32 planes for V > 1 shells (the
+// plain kernel); float2 pair words for every other FP32 run, one particle
+// included (its clusters paired in the words).
 int run_layout(const ifcm_params* p, int P_total) {
+  (void)P_total;
   if (is_bf16(p)) return UL_BF16;
-  if (p->V > 1 || P_total < 2) return UL_PLANAR;
+  if (p->V > 1) return UL_PLANAR;
   return UL_F32P;
 }
 
@@ -195,29 +196,36 @@ struct RunBufs {
   RunState st;
 };
 
-// 4-byte elements per voxel of one membership buffer of P particles.
-size_t run_buffer_elems(int c, int P, int layout) {
+// 4-byte elements per voxel of one membership buffer of P particles; pairs2:
+// the batch (two or more particles) may run two particles per item.
+size_t run_buffer_elems(int c, int P, int layout, bool pairs2) {
   if (layout == UL_PLANAR) return static_cast<size_t>(P) * c;
   long long w = pair_unit_words(c, 1, P);
-  if (c <= 5 && pair_unit_words(c, 2, P) > w) w = pair_unit_words(c, 2, P);
+  if (pairs2 && c <= 5 && pair_unit_words(c, 2, P) > w) w = pair_unit_words(c, 2, P);
   if (layout == UL_F32P) w *= 2;          // 8-byte words
   // the FCM start (FP32 planes, one particle) also runs in these buffers
   if (w < c) w = c;
   return static_cast<size_t>(w);
 }
 
+int forced_np();
+
 RunBufs carve_runs(Carver& cv, const ifcm_shape* shapes, const int* P, int n, int c,
                    int layout) {
   RunBufs r{};
   r.n = n;
   r.layout = layout;
+  int P_total = 0;
+  for (int v = 0; v < n; ++v) P_total += P[v];
+  const bool pairs2 = P_total >= 2 || forced_np() == 2;
   long long recs = 0;
   int pb = 0;
   for (int v = 0; v < n; ++v) {
     const size_t pl = plane_elems(shapes[v]);
-    r.buf_elems[v] = static_cast<long long>(run_buffer_elems(c, P[v], layout) * pl);
-    r.ua[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
-    r.ub[v] = cv.take<float>(run_buffer_elems(c, P[v], layout) * pl);
+    const size_t be = run_buffer_elems(c, P[v], layout, pairs2) * pl;
+    r.buf_elems[v] = static_cast<long long>(be);
+    r.ua[v] = cv.take<float>(be);
+    r.ub[v] = cv.take<float>(be);
     r.u0p[v] = layout == UL_PLANAR ? nullptr
                : cv.take<float>(static_cast<size_t>(c) * pl * (layout == UL_F32P ? 2 : 1));
     r.gs[v] = cv.take<float>(pl);
@@ -487,6 +495,12 @@ struct Tuner {
   std::map<std::vector<long long>, StencilPlan> cache;
 } g_tune;
 
+// Particles per item of the forced plan, 0 when none is forced.
+int forced_np() {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  return g_tune.force.np;
+}
+
 // Cache key: element type of the memberships (an IFCM_U_* value), c, and
 // every volume's extent and particle count.
 std::vector<long long> plan_key(const BatchVol* vols, int n, int c, int u_dtype) {
@@ -586,7 +600,9 @@ ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const R
   const StencilPlan h = heuristic_plan(vols, n, c, lay);
   const int kmax = most_chunks(vols, n);
   std::vector<StencilPlan> cand;
-  for (int np = 1; np <= 2; ++np) {
+  int P_total = 0;
+  for (int v = 0; v < n; ++v) P_total += vols[v].P;
+  for (int np = 1; np <= (P_total >= 2 ? 2 : 1); ++np) {
     if (!stencil_np_supported(c, np)) continue;
     for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
       if (k > kmax) break;
@@ -632,8 +648,22 @@ ifcm_status tune_plan(const BatchVol* vols, int n, const ifcm_params* p, const R
   return rc;
 }
 
+ifcm_status choose_plan_any(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
+                            DevStatus* status, cudaStream_t st, StencilPlan* out);
+
+// The plan of a batch; a single particle runs one per item (its buffers hold
+// no second particle) unless a plan is forced.
 ifcm_status choose_plan(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
                         DevStatus* status, cudaStream_t st, StencilPlan* out) {
+  ST_TRY(choose_plan_any(vols, n, p, rb, status, st, out));
+  int P_total = 0;
+  for (int v = 0; v < n; ++v) P_total += vols[v].P;
+  if (P_total < 2 && forced_np() == 0) out->np = 1;
+  return IFCM_OK;
+}
+
+ifcm_status choose_plan_any(const BatchVol* vols, int n, const ifcm_params* p, const RunBufs& rb,
+                            DevStatus* status, cudaStream_t st, StencilPlan* out) {
   const std::vector<long long> key = plan_key(vols, n, p->c, p->u_dtype);
   int mode;
   {
@@ -1185,7 +1215,7 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
   BatchVol bv{};
   bv.shape = shape;
   bv.P = P;
-  StencilPlan pl = heuristic_plan(&bv, 1, c, P >= 2 ? UL_F32P : UL_PLANAR);
+  StencilPlan pl = heuristic_plan(&bv, 1, c, UL_F32P);
   int32_t tuned = 0;
   {
     std::lock_guard<std::mutex> lk(g_tune.mu);
@@ -1197,6 +1227,7 @@ int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, i
       tuned = 1;
     }
   }
+  if (P < 2 && forced_np() == 0) pl.np = 1;
   if (np) *np = pl.np;
   if (tz) *tz = tiling(shape, pl.chunks).tz;
   return tuned;

@@ -14,7 +14,7 @@ cudaError_t launch_np2(const StencilArgs& a, int grid, cudaStream_t s) {
   for (int v = 0; v < a.n_vol; ++v)
     deep = deep || stencil3d_eligible(UL_F32P, 2, a.m_is_2, a.sum_one, a.vol[v].nz);
   if (!deep) return launch_c<C, 2, UL_F32P>(a, grid, s);
-  cudaError_t e = launch3d_c<C>(a, grid, s);
+  cudaError_t e = launch3d_c<C, 2>(a, grid, s);
   if (e != cudaSuccess) return e;
   return launch_c<C, 2, UL_F32P>(a, grid, s, false);    // the 2D images of the batch
 }

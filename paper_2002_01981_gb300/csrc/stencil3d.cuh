@@ -1,13 +1,15 @@
-// Batched IFCM iteration over 3D volumes, two particles per work item, FP32
-// memberships in float2 pair words, m = 2: the neighbourhood stencil of Eqs
-// 5-9 fused with Eq 4 (distance), Eq 2 (membership), Eq 1 (objective) and the
-// centre sums of Eq 3.  This is the form of the batched fitness evaluation
-// (Algorithm 1 step 4) that carries almost all of a run's time; every other
-// case (2D images, m != 2, one particle, bf16 words, the first iteration from
-// a caller's start) runs stencil_kernel (stencil_kernel.cuh).
+// Batched IFCM iteration over 3D volumes, FP32 memberships in float2 pair
+// words, m = 2: the neighbourhood stencil of Eqs 5-9 fused with Eq 4
+// (distance), Eq 2 (membership), Eq 1 (objective) and the centre sums of Eq 3.
+// This is the form of the batched fitness evaluation (Algorithm 1 step 4) that
+// carries almost all of a run's time.  A pair word holds cluster j of the
+// item's two particles (NP = 2, c <= 5) or clusters 2k, 2k+1 of its one
+// particle (NP = 1, any c).  Every other case (2D images, m != 2, planar or
+// bf16 memberships, the first iteration from a caller's start) runs
+// stencil_kernel (stencil_kernel.cuh).
 //
 // Work decomposition, ring and producer are those of stencil_kernel: items of
-// (pair of particles, 32 x TY column tile, z-chunk), a TMA producer warp
+// (pair-word unit, 32 x TY column tile, z-chunk), a TMA producer warp
 // feeding an 8-stage ring of planes, one consumer thread per column marching
 // up z.  What differs is the consumer's plane step, written for the fewest
 // instructions per update:
@@ -25,10 +27,12 @@
 //   2) - x_i|, which turns H into the plain mean, with no branch.
 // - Memberships of one voxel sum to one (Eq 2), so sum_j H_ij = 1 and the last
 //   cluster's H is 1 - sum_{j<c-1} H_ij: its 26 neighbour products are not
-//   formed.  U^t always comes from Eq 2 here (iteration 0, which reads the
-//   caller's start, runs stencil_kernel).
+//   formed, wherever that saves a whole pair word (NP = 2, or NP = 1 with c
+//   odd, whose last word holds cluster c - 1 and a padding lane).  U^t always
+//   comes from Eq 2 here (iteration 0, which reads the caller's start, runs
+//   stencil_kernel).
 // - F needs no per-centre accumulation across planes beyond one float2 per
-//   cluster: each plane's window sums W0 (centre), S1 (faces), S2 (corners) of
+//   pair word: each plane's window sums W0 (centre), S1 (faces), S2 (corners) of
 //   u^2 give A = W0 + 2 S1 + 3 S2 (weight 1 + dx^2 + dy^2, to the centres
 //   above and below) and V = S1 + 2 S2 (weight dx^2 + dy^2, to the centre in
 //   the plane).
@@ -52,17 +56,27 @@ namespace {
 
 constexpr int SBYTES = ((TX * TY * 4 + 127) / 128) * 128;   // 1/G of the tile's centres
 
-template <int C>
+// Pair words per voxel (K), H sums kept (KH), and whether the last cluster's H
+// is taken by complement (COMPL) and the last word's high lane is padding (PAD).
+template <int C, int NP>
+struct S3 {
+  static constexpr int K = Pairs<C, NP>::K;
+  static constexpr bool PAD = NP == 1 && (C & 1);
+  static constexpr bool COMPL = NP == 2 || PAD;
+  static constexpr int KH = COMPL ? K - 1 : K;
+};
+
+template <int C, int NP>
 __host__ __device__ constexpr int s3_stage_bytes() {
-  return XBYTES + SBYTES + ublock_bytes<C, 2, UL_F32P>();
+  return XBYTES + SBYTES + ublock_bytes<C, NP, UL_F32P>();
 }
-template <int C>
+template <int C, int NP>
 __host__ __device__ constexpr uint32_t s3_tx_bytes() {
-  return static_cast<uint32_t>(PLANE * 4 + TX * TY * 4 + C * PLANE * 8);
+  return static_cast<uint32_t>(PLANE * 4 + TX * TY * 4 + S3<C, NP>::K * PLANE * 8);
 }
-template <int C>
+template <int C, int NP>
 __host__ __device__ constexpr int s3_smem_total() {
-  return NSTAGE * s3_stage_bytes<C>() + 128;
+  return NSTAGE * s3_stage_bytes<C, NP>() + 128;
 }
 static_assert(NSTAGE == 8, "stage indices are taken modulo 8 with a mask");
 static_assert(SBYTES % 128 == 0, "TMA destinations start on 128-byte boundaries");
@@ -72,12 +86,13 @@ static_assert(SBYTES % 128 == 0, "TMA destinations start on 128-byte boundaries"
 static_assert(BX + 4 - BX - 1 >= 0 && TY * BX + TX - 1 + 4 + BX + 1 < PLANE,
               "stencil reads stay inside the stage plane");
 
-// One centre of the column: its sums over the planes read so far.
-template <int C>
+// One centre of the column: its sums over the planes read so far, one float2
+// per pair word.
+template <int C, int NP>
 struct Slot3 {
-  static constexpr int KH = C - 1;   // clusters whose H is summed (the last by complement)
-  float2 H[KH];                      // sum_k u_kj g_ik, pair = the item's two particles
-  float2 F[C];                       // sum_k u_kj^2 q^2_ik
+  static constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
+  float2 H[KH];                      // sum_k u_kj g_ik (the last cluster's by complement)
+  float2 F[K];                       // sum_k u_kj^2 q^2_ik
   float x;                           // x_i
   float s;                           // 1/G_i, or -1/(n_i g0) for a flat neighbourhood
   float xg;                          // x_i in g_ik: x_i, or x_i + 2 for a flat neighbourhood
@@ -85,26 +100,29 @@ struct Slot3 {
 #pragma unroll
     for (int q = 0; q < KH; ++q) H[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int q = 0; q < C; ++q) F[q] = make_float2(0.0f, 0.0f);
+    for (int q = 0; q < K; ++q) F[q] = make_float2(0.0f, 0.0f);
     x = s = xg = 0.0f;
   }
 };
 
 // Constants of an item, paired like the sums.
-template <int C>
+template <int C, int NP>
 struct Fin3 {
-  float2 ncc[C];                     // -c_j of the two particles
-  float2 nlam, nxi;                  // -lambda, -xi of the two particles
+  float2 ncc[S3<C, NP>::K];          // -c_j, paired like the sums (0 in a padding lane)
+  float2 nlam, nxi;                  // -lambda, -xi of the lanes' particles
   float floor;                       // dist_floor
 };
 
-template <int C>
+// A thread's shares of the item's sums; with one particle, J and max|du| are
+// in the low lane.
+template <int C, int NP>
 struct Acc3 {
-  float2 s0[C], s1[C];               // sum u^m, sum u^m x
-  float2 J, dm;                      // J, max|du| of the two particles
+  static constexpr int K = S3<C, NP>::K;
+  float2 s0[K], s1[K];               // sum u^m, sum u^m x
+  float2 J, dm;                      // J, max|du|
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int q = 0; q < C; ++q) s0[q] = s1[q] = make_float2(0.0f, 0.0f);
+    for (int q = 0; q < K; ++q) s0[q] = s1[q] = make_float2(0.0f, 0.0f);
     J = dm = make_float2(0.0f, 0.0f);
   }
 };
@@ -114,50 +132,65 @@ struct Acc3 {
 // Eq 2 for m = 2, the U^{t+1} store and the centre's shares of Eqs 1 and 3
 // and of max|du|.  ud: the centre's U^t in its stage (pair words at its
 // column); dst: its U^{t+1} word of pair 0.
-template <int C>
-__device__ __forceinline__ void fin3(const Slot3<C>& d, const float2* __restrict__ ud, float invq,
-                                     const Fin3<C>& fc, Acc3<C>& acc, float2* __restrict__ dst,
-                                     int plane, bool st) {
-  constexpr int KH = C - 1;
+template <int C, int NP>
+__device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __restrict__ ud,
+                                     float invq, const Fin3<C, NP>& fc, Acc3<C, NP>& acc,
+                                     float2* __restrict__ dst, int plane, bool st) {
+  constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
   const float ig = fabsf(d.s);
-  float2 hs = d.H[0];
-#pragma unroll
-  for (int q = 1; q < KH; ++q) hs = __fadd2_rn(hs, d.H[q]);
   // f_j = 1 - lambda H_j - xi F_j with H_j = Hs_j / G and F_j = Fs_j / Q,
   // taking -lambda / G and -xi / Q once per centre
   const float2 nl = __fmul2_rn(fc.nlam, dup2(ig)), nx = __fmul2_rn(fc.nxi, dup2(invq));
-  float2 fq[C];
+  float2 fq[K];
 #pragma unroll
   for (int q = 0; q < KH; ++q) fq[q] = __ffma2_rn(nx, d.F[q], __ffma2_rn(nl, d.H[q], dup2(1.0f)));
-  // the last cluster: 1 - lambda (1 - sum_{j<c-1} H_j) - xi F
-  fq[C - 1] = __ffma2_rn(nx, d.F[C - 1], __ffma2_rn(__fmul2_rn(nl, dup2(-1.0f)), hs,
-                                                    __fadd2_rn(dup2(1.0f), fc.nlam)));
-  // Eq 4 (reading R2): max(D max(f, 0), floor) = max(D f, floor) for D >= 0
-  float2 r[C];
+  if (S3<C, NP>::COMPL) {
+    // the last cluster: 1 - lambda (1 - sum_{j<c-1} H_j) - xi F, with the
+    // other clusters' sums of its particle (per lane for NP = 2; both lanes
+    // of every other word for NP = 1, whose last word's high lane is padding)
+    float2 hs = d.H[0];
 #pragma unroll
-  for (int q = 0; q < C; ++q) {
-    const float2 f = fq[q];
+    for (int q = 1; q < KH; ++q) hs = __fadd2_rn(hs, d.H[q]);
+    if (NP == 1) hs = dup2(hs.x + hs.y);
+    fq[K - 1] = __ffma2_rn(nx, d.F[K - 1], __ffma2_rn(__fmul2_rn(nl, dup2(-1.0f)), hs,
+                                                      __fadd2_rn(dup2(1.0f), fc.nlam)));
+  }
+  // Eq 4 (reading R2): max(D max(f, 0), floor) = max(D f, floor) for D >= 0
+  float2 r[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
     const float2 dd = __fadd2_rn(dup2(d.x), fc.ncc[q]);
-    const float2 d2 = max2(__fmul2_rn(__fmul2_rn(dd, dd), f), fc.floor);
+    const float2 d2 = max2(__fmul2_rn(__fmul2_rn(dd, dd), fq[q]), fc.floor);
     r[q] = make_float2(fast_rcp(d2.x), fast_rcp(d2.y));
   }
+  if (S3<C, NP>::PAD) r[K - 1].y = 0.0f;     // the padding lane is no cluster
   // Eq 2 with m = 2: u_j = (1/d2_j) / S, S = sum_k 1/d2_k; Eq 1 share = 1/S
   float2 S = r[0];
 #pragma unroll
-  for (int q = 1; q < C; ++q) S = __fadd2_rn(S, r[q]);
-  const float2 inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
-  acc.J = __fadd2_rn(acc.J, inv);
+  for (int q = 1; q < K; ++q) S = __fadd2_rn(S, r[q]);
+  float2 inv;
+  if (NP == 2) {
+    inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
+    acc.J = __fadd2_rn(acc.J, inv);
+  } else {
+    inv = dup2(fast_rcp(S.x + S.y));
+    acc.J.x += inv.x;
+  }
   const float2 x2 = dup2(d.x);
 #pragma unroll
-  for (int q = 0; q < C; ++q) {
+  for (int q = 0; q < K; ++q) {
     const float2 u = __fmul2_rn(r[q], inv);
     const float2 um = __fmul2_rn(u, u);
     acc.s0[q] = __fadd2_rn(acc.s0[q], um);
     acc.s1[q] = __ffma2_rn(um, x2, acc.s1[q]);
     if (st) __stcg(&dst[q * plane], u);
     const float2 e = __ffma2_rn(ud[q * PLANE], dup2(-1.0f), u);   // u' - u
-    acc.dm.x = fmaxf(acc.dm.x, fabsf(e.x));
-    acc.dm.y = fmaxf(acc.dm.y, fabsf(e.y));
+    if (NP == 2) {
+      acc.dm.x = fmaxf(acc.dm.x, fabsf(e.x));
+      acc.dm.y = fmaxf(acc.dm.y, fabsf(e.y));
+    } else {
+      acc.dm.x = fmaxf(acc.dm.x, fmaxf(fabsf(e.x), fabsf(e.y)));
+    }
   }
 }
 
@@ -165,19 +198,19 @@ __device__ __forceinline__ void fin3(const Slot3<C>& d, const float2* __restrict
 // plane pz to centres pz - 1 (l), pz (m) and pz + 1 (h, whose sums start
 // here; its x and s come from stage pz + 1).  xs / us: stage pz at the
 // column; xn / sn: stage pz + 1 at the column; ud: stage pz - 2 at the column.
-template <int C, bool FIN>
+template <int C, int NP, bool FIN>
 __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2* __restrict__ us,
                                       const float* __restrict__ xn, const float* __restrict__ sn,
-                                      const float2* __restrict__ ud, Slot3<C>& d, Slot3<C>& l,
-                                      Slot3<C>& m, Slot3<C>& h, float invq, const Fin3<C>& fc,
-                                      Acc3<C>& acc, float2* __restrict__ dst, int plane,
-                                      bool st) {
-  constexpr int KH = C - 1;
+                                      const float2* __restrict__ ud, Slot3<C, NP>& d,
+                                      Slot3<C, NP>& l, Slot3<C, NP>& m, Slot3<C, NP>& h,
+                                      float invq, const Fin3<C, NP>& fc, Acc3<C, NP>& acc,
+                                      float2* __restrict__ dst, int plane, bool st) {
+  constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
   h.x = xn[0];
   h.s = sn[0];
   h.xg = h.s < 0.0f ? h.x + 2.0f : h.x;
-  if (FIN) fin3<C>(d, ud, invq, fc, acc, dst, plane, st);
-  float2 W0[C], S1[C], S2[C];
+  if (FIN) fin3<C, NP>(d, ud, invq, fc, acc, dst, plane, st);
+  float2 W0[K], S1[K], S2[K];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
@@ -192,7 +225,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
       const float gh = fabsf(h.xg - xk);
       const float gm = self ? 0.0f : fabsf(m.xg - xk);
 #pragma unroll
-      for (int q = 0; q < C; ++q) {
+      for (int q = 0; q < K; ++q) {
         const float2 uk = us[q * PLANE + off];
         if (q < KH) {
           l.H[q] = __ffma2_rn(uk, dup2(gl), l.H[q]);
@@ -206,7 +239,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
     }
   }
 #pragma unroll
-  for (int q = 0; q < C; ++q) {
+  for (int q = 0; q < K; ++q) {
     const float2 V = __ffma2_rn(dup2(2.0f), S2[q], S1[q]);                          // S1 + 2 S2
     const float2 A = __ffma2_rn(dup2(3.0f), S2[q], __ffma2_rn(dup2(2.0f), S1[q], W0[q]));
     l.F[q] = __fadd2_rn(l.F[q], A);
@@ -215,34 +248,39 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
   }
 }
 
-template <int C>
+template <int C, int NP>
 __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant__ StencilArgs a) {
+  constexpr int K = S3<C, NP>::K;
   extern __shared__ unsigned char dsmem_raw[];
   __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ uint32_t lastq[NSTAGE];    // the last plane loaded into each stage
   __shared__ __align__(8) uint64_t empty[NSTAGE];
   __shared__ ItemTable tab;
   __shared__ int s_abort;
-  __shared__ float s_red[NCW][2 * (2 * C + 2)];
-  __shared__ ItemConst<C, 2> s_ic;
+  __shared__ float s_red[NCW][NP * (2 * C + 2)];
+  __shared__ ItemConst<C, NP> s_ic;
 
   // 128-byte aligned start by pointer arithmetic, so that the compiler keeps
   // the shared address space of every stage pointer
   unsigned char* dsmem = dsmem_raw + ((128u - (smem_addr(dsmem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  constexpr int SB = s3_stage_bytes<C>();
+  constexpr int SB = s3_stage_bytes<C, NP>();
   const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
-  // Active pairs of every volume, compacted one volume per warp (ballots).
+  // Active units of every volume (pairs (2k, 2k+1) active while either runs,
+  // or particles), compacted one volume per warp (ballots).
   for (int v = warp; v < a.n_vol; v += NT / 32) {
     const VolDesc& vd = a.vol[v];
-    const int units = vd.nz == 1 ? 0 : (vd.P + 1) / 2;
+    const int units = vd.nz == 1 ? 0 : NP == 2 ? (vd.P + 1) / 2 : vd.P;
     int n = 0;
     for (int base = 0; base < units; base += 32) {
       const int p = base + lane;
-      const bool on = p < units && (a.active[vd.pbase + 2 * p] != 0 ||
-                                    (2 * p + 1 < vd.P && a.active[vd.pbase + 2 * p + 1] != 0));
+      const bool on =
+          p < units &&
+          (NP == 2 ? (a.active[vd.pbase + 2 * p] != 0 ||
+                      (2 * p + 1 < vd.P && a.active[vd.pbase + 2 * p + 1] != 0))
+                   : a.active[vd.pbase + p] != 0);
       const unsigned msk = __ballot_sync(0xffffffffu, on);
       const int ia = vd.pbase + n + __popc(msk & ((1u << lane) - 1u));
       if (on && IFCM_CHECK(ia >= 0 && ia < kMaxBatchParticles, a.status, 30))
@@ -280,12 +318,12 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   auto load_plane = [&](uint32_t qq, const Item& it, int pz) {
     const VolDesc& vd = a.vol[it.v];
     const uint32_t s = qq & (NSTAGE - 1);
-    if (!IFCM_CHECK(pz >= 0 && pz < vd.nz && it.unit * vd.src_cstride + C <= vd.src_planes,
+    if (!IFCM_CHECK(pz >= 0 && pz < vd.nz && it.unit * vd.src_cstride + K <= vd.src_planes,
                     a.status, 31))
       return;
     unsigned char* st = dsmem + s * SB;
     lastq[s] = qq;
-    mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C>());
+    mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C, NP>());
     tma_load_3d(st, &a.tm_x[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz);
     tma_load_3d(st + XBYTES, &a.tm_s[it.v], &full[s], it.x0, it.y0, pz);
     tma_load_4d(st + XBYTES + SBYTES, &a.tm_u[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz,
@@ -299,7 +337,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       uint32_t q = 0;
       bool go = true;
       for (int w = blockIdx.x; go && w < n_items; w += gridDim.x) {
-        const Item it = decode_item<2, UL_F32P>(a, tab, w);
+        const Item it = decode_item<NP, UL_F32P>(a, tab, w);
         for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
           const uint32_t s = q & (NSTAGE - 1);
           if (q >= NSTAGE && !mbar_wait_bounded(&empty[s], ((q / NSTAGE) - 1) & 1, wait_ns)) {
@@ -352,7 +390,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   };
 
   for (int w = blockIdx.x; warp < NCW && w < n_items; w += gridDim.x) {
-    const Item it = decode_item<2, UL_F32P>(a, tab, w);
+    const Item it = decode_item<NP, UL_F32P>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
     const uint32_t q0 = q;
     const int plane = vd.nz * vd.ny * vd.pitch;
@@ -362,21 +400,23 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       float lam[2], xi[2], cc[2][C];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const int pid = p == 0 ? it.p0 : it.p1;
+        const int pid = (p == 0 || NP == 1) ? it.p0 : it.p1;
         lam[p] = static_cast<float>(vd.lam_xi[2 * pid]);
         xi[p] = static_cast<float>(vd.lam_xi[2 * pid + 1]);
 #pragma unroll
         for (int j = 0; j < C; ++j)
           cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
       }
-      s_ic.dst[0] = vd.u_dst + static_cast<size_t>(it.unit) * C * plane * 2;
+      s_ic.dst[0] = vd.u_dst + static_cast<size_t>(it.unit) * K * plane * 2;
       s_ic.nlam = make_float2(-lam[0], -lam[1]);
       s_ic.nxi = make_float2(-xi[0], -xi[1]);
 #pragma unroll
-      for (int j = 0; j < C; ++j) s_ic.ncc[j] = make_float2(-cc[0][j], -cc[1][j]);
+      for (int q = 0; q < K; ++q)
+        s_ic.ncc[q] = NP == 2 ? make_float2(-cc[0][q], -cc[1][q])
+                              : make_float2(-cc[0][2 * q], 2 * q + 1 < C ? -cc[0][2 * q + 1] : 0.0f);
     }
     consumer_sync();
-    Acc3<C> acc;
+    Acc3<C, NP> acc;
     acc.clear();
 
     {
@@ -387,9 +427,9 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
         box_counts(cx.X, cx.Y, 0, vd.nx, vd.ny, vd.nz, cnt, Q);
         iqz = cnt > 0 ? __frcp_rn(Q) : 0.0f;
       }
-      Fin3<C> fc;
+      Fin3<C, NP> fc;
 #pragma unroll
-      for (int j = 0; j < C; ++j) fc.ncc[j] = s_ic.ncc[j];
+      for (int q = 0; q < K; ++q) fc.ncc[q] = s_ic.ncc[q];
       fc.nlam = s_ic.nlam;
       fc.nxi = s_ic.nxi;
       fc.floor = a.dist_floor;
@@ -397,13 +437,13 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       // stores of the column (the item's centres lie in [z0, z1) of the volume)
       const bool st = cx.col_ok &&
                       IFCM_CHECK(it.z0 >= 0 && it.z1 <= vd.nz &&
-                                     (static_cast<long long>(it.unit) + 1) * C * plane * 2 <=
+                                     (static_cast<long long>(it.unit) + 1) * K * plane * 2 <=
                                          vd.dst_elems,
                                  a.status, 32);
       float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
       const int zstride = vd.ny * vd.pitch;
 
-      Slot3<C> s0, s1, s2, s3;
+      Slot3<C, NP> s0, s1, s2, s3;
       // the first step whose delayed finalisation is a centre of the item
       const int kf = it.z0 - it.pzb + 2;
       // the generic step covers the steps before the first interior-z centre
@@ -432,10 +472,10 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
           const float invq = zd == 0 ? iqz : iqc;
           float2* dst = col_dst + static_cast<long long>(zd) * zstride;
           if (kk >= kf)
-            step3<C, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
+            step3<C, NP, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
                            s1, s2, s3, invq, fc, acc, dst, plane, st);
           else
-            step3<C, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6),
+            step3<C, NP, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6),
                             s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
         }
         if (!landed2) ok = ok && wait_full(qq + 2);
@@ -457,11 +497,11 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
           const uint32_t qr = qq + r;
           const bool landed2 =
               mbar_test_wait(&full[(qr + 2) & (NSTAGE - 1)], ((qr + 2) / NSTAGE) & 1);
-          Slot3<C>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
-          Slot3<C>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
-          Slot3<C>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
-          Slot3<C>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
-          step3<C, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l,
+          Slot3<C, NP>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
+          Slot3<C, NP>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
+          Slot3<C, NP>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
+          Slot3<C, NP>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
+          step3<C, NP, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l,
                          m, h, iqc, fc, acc, dst + r * zstride, plane, st);
           if (!landed2) ok = ok && wait_full(qr + 2);
           release(qr - 2);
@@ -475,10 +515,10 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       const bool live = ok && !*reinterpret_cast<volatile int*>(&s_abort);
       const int zl = it.pze - 1;
       if (live && np >= 2 && zl >= it.z0 && zl < it.z1)
-        fin3<C>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
+        fin3<C, NP>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
                 col_dst + static_cast<long long>(zl) * zstride, plane, st);
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1)
-        fin3<C>(s1, us_at(ql), iqz, fc, acc, col_dst + static_cast<long long>(it.pze) * zstride,
+        fin3<C, NP>(s1, us_at(ql), iqz, fc, acc, col_dst + static_cast<long long>(it.pze) * zstride,
                 plane, st);
       if (np >= 2) release(ql - 1);
       release(ql);
@@ -488,11 +528,14 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
 
     // Item partial sums: FP32 within a thread and a warp, FP64 across warps.
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < NP; ++p) {
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const float v0 = warp_sum(p == 0 ? acc.s0[j].x : acc.s0[j].y);
-        const float v1 = warp_sum(p == 0 ? acc.s1[j].x : acc.s1[j].y);
+        // cluster j of particle p: lane p of word j (NP = 2), lane j % 2 of word j / 2
+        const bool hi = NP == 2 ? p == 1 : (j & 1);
+        const int q = NP == 2 ? j : j >> 1;
+        const float v0 = warp_sum(hi ? acc.s0[q].y : acc.s0[q].x);
+        const float v1 = warp_sum(hi ? acc.s1[q].y : acc.s1[q].x);
         if (lane == 0) {
           s_red[warp][p * (2 * C + 2) + j] = v0;
           s_red[warp][p * (2 * C + 2) + C + j] = v1;
@@ -506,7 +549,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       }
     }
     consumer_sync();
-    if (tid < 2 * (2 * C + 2)) {
+    if (tid < NP * (2 * C + 2)) {
       const int p = tid / (2 * C + 2), v = tid - p * (2 * C + 2);
       if (p == 0 ? it.on0 : it.two) {
         const int pid = p == 0 ? it.p0 : it.p1;
@@ -545,14 +588,14 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   }
 }
 
-// One launch of the 3D float2-pair kernel (every volume of `a` is 3D).
-template <int C>
+// One launch of the 3D float2-pair kernel (it takes the 3D volumes of `a`).
+template <int C, int NP>
 cudaError_t launch3d_c(const StencilArgs& a, int grid, cudaStream_t s) {
-  constexpr int smem = s3_smem_total<C>();
-  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C>,
+  constexpr int smem = s3_smem_total<C, NP>();
+  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C, NP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil3d_kernel<C><<<grid, NT, smem, s>>>(a);
+  stencil3d_kernel<C, NP><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
