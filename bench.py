@@ -161,12 +161,12 @@ def stencil_traffic_per_update(plan_np, plan_tz):
 
 def launches_per_run(init_iters_launched, generations, max_iter):
     # normalise (2) + FCM start (state init + 2 per iteration + copy) + swarm
-    # init + per generation (state init + 1/G of the volume + start packing
-    # into pair words + 2 per iteration + swarm step) + best + final run (state
-    # init + 1/G + start packing + 2 per iteration + copy) + result.
-    return (2 + 1 + 2 * init_iters_launched + 1 + 1 +
-            generations * (1 + 1 + 1 + 2 * max_iter + 1) + 1 +
-            (1 + 1 + 1 + 2 * max_iter + 1) + 1)
+    # init + 1/G of the volume (once) + per generation (state init + start
+    # packing into pair words + 2 per iteration + swarm step) + best + final
+    # run (state init + start packing + 2 per iteration + copy) + result.
+    return (2 + 1 + 2 * init_iters_launched + 1 + 1 + 1 +
+            generations * (1 + 1 + 2 * max_iter + 1) + 1 +
+            (1 + 1 + 2 * max_iter + 1) + 1)
 
 
 def plain_form_rate(G, vol, nx, prm, opts, stream, particles=2):
@@ -284,10 +284,11 @@ def batching_leg(G, phantoms, dev):
 
 # ------------------------------------------- membership storage precision
 PREC_SHAPE = (256, 256, 256)
-PREC_C, PREC_P = 6, 64
+PREC_C, PREC_P, PREC_GEN = 6, 64, 40
 PREC_WORKLOAD = ("background + 5 tissues 256^3 (0/0.2/0.35/0.5/0.7/0.9), Rician sigma 0.1, c=6, "
                  "m=2, 26-neighbourhood, one generation of 64 particles (swarm init, seed 5), "
-                 f"<= {MAX_ITER} IFCM iterations per fitness, stop max|du|<{EPS:g}")
+                 f"<= {MAX_ITER} IFCM iterations per fitness, stop max|du|<{EPS:g}; full_run: "
+                 f"one whole Algorithm 1 run of {PREC_P} particles x {PREC_GEN} generations")
 
 
 def precision_leg(G, phantoms, dev):
@@ -305,7 +306,6 @@ def precision_leg(G, phantoms, dev):
     vol = torch.from_numpy(phantoms.pad_pitch(raw)).to(dev)
     del raw
     x = G.ifcm_normalize(vol, nx=nx)
-    del vol
     U0, C0, _, it0 = G.ifcm_fit(x, G.Params(c=PREC_C, m=M, max_iter=INIT_MAX_ITER, eps_u=EPS),
                                 (0.0, 0.0), nx=nx)
     sw = G.Swarm(PREC_P, seed=5).init()
@@ -368,6 +368,47 @@ def precision_leg(G, phantoms, dev):
         v["over_fp32"] = v["value"] / v32
     del ws, x, U0
     torch.cuda.empty_cache()
+    out["full_run"] = precision_full_runs(G, vol, nx)
+    del vol
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_full_runs(G, vol, nx):
+    """The c = 6 workload as stated: one whole Algorithm 1 run of 64 particles
+    x 40 generations (<= 50 iterations each, FCM start <= 300 iterations),
+    with FP32 and with bf16 memberships (FP64 sums): seconds, updates/s, the
+    best (lambda, xi), and the bf16 run's final segmentation against the FP32
+    run's (labels, centres, J)."""
+    import torch
+    opts = G.Options(P=PREC_P, generations=PREC_GEN, seed=5, init_max_iter=INIT_MAX_ITER)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    out, ref = {}, None
+    for d in ("fp32", "bf16"):
+        prm = G.Params(c=PREC_C, m=M, max_iter=MAX_ITER, eps_u=EPS, u_dtype=d)
+        bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
+        torch.cuda.synchronize()
+        ev0.record()
+        U, res = G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs)
+        ev1.record()
+        torch.cuda.synchronize()
+        s = ev0.elapsed_time(ev1) / 1e3
+        lab = torch.argmax(U[..., :nx], dim=0)
+        r = {"seconds": s, "updates": int(res["updates"]), "value": res["updates"] / s,
+             "unit": UNIT, "lambda_xi": [res["lambda"], res["xi"]], "J": res["J"],
+             "best_fitness": res["best_fitness"], "iters_final": res["iters_final"]}
+        if ref is None:
+            ref = (lab, np.asarray(res["centres"][:PREC_C]), res["J"], r["value"])
+        else:
+            r["vs_fp32"] = {"labels_agree": float((lab == ref[0]).double().mean()),
+                            "centres_max_rel": float(np.max(np.abs(
+                                np.asarray(res["centres"][:PREC_C]) / ref[1] - 1.0))),
+                            "J_rel": abs(res["J"] / ref[2] - 1.0),
+                            "over_fp32": r["value"] / ref[3]}
+        out[d] = r
+        del U, bufs, lab
+        torch.cuda.empty_cache()
     return out
 
 
@@ -702,7 +743,9 @@ def run_ours(args):
     vol = vol_host.to(dev)
     n_p, n_gen, n_it, n_init = P, GENERATIONS, MAX_ITER, INIT_MAX_ITER
     if args.small:       # short case for profiler captures: same volume and kernels
-        n_p, n_gen, n_it, n_init = P, 1, 3, 3
+        n_p, n_gen, n_it, n_init = args.small_particles or P, 1, 3, 3
+        if args.small_particles:
+            G.force_plan(2, 1)        # the full run's plan: 2 particles per item, whole columns
     prm = G.Params(c=C, m=M, max_iter=n_it, eps_u=EPS)
     opts = G.Options(P=n_p, generations=n_gen, seed=rank_seed(rank), init_max_iter=n_init)
     bufs = G.pifcm3d_buffers(vol, prm, opts, nx=nx)
@@ -738,9 +781,10 @@ def run_ours(args):
     _, res = G.pifcm3d(vol, prm, opts, nx=nx, buffers=bufs)   # same work every step
     updates_step = res["updates"]
     init_updates = res["iters_init"] * N
-    # stencil3d_kernel runs every batch iteration after the first; the first
-    # (all particles) and the one-particle final run use stencil_kernel
-    k3_updates_step = updates_step - init_updates - n_gen * n_p * N - res["iters_final"] * N
+    # stencil3d_kernel runs every iteration of the batches (two particles per
+    # item) and of the final run (one particle, clusters paired)
+    final_updates = res["iters_final"] * N
+    k3_updates_step = updates_step - init_updates
 
     s_max, total_updates = reduce_over_ranks(dist, world, ms / 1e3, updates_step * args.steps,
                                              dev)
@@ -781,14 +825,19 @@ def run_ours(args):
     # U^t read + U^{t+1} write + x read once per item, shared by the item's particles
     plan_np, plan_tz, _ = G.stencil_plan(G.shape_of(vol, nx), C, P)
     bytes_per_update = 2 * C * 4 + 4.0 / plan_np
+    step_bytes = ((k3_updates_step - final_updates) * bytes_per_update +
+                  final_updates * (2 * C * 4 + 4.0))
     per_launch_updates = k3_updates_step * args.steps / max(k3_launches, 1)
-    achieved = (k3_updates_step * args.steps * bytes_per_update) / (k3_ms / 1e3) / 1e9
+    achieved = step_bytes * args.steps / (k3_ms / 1e3) / 1e9
     traffic_pu = stencil_traffic_per_update(plan_np, plan_tz)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_kind": peak_kind,
                 "traffic": traffic_pu * per_launch_updates if traffic_pu else None,
-                "algorithmic_bytes_per_launch": per_launch_updates * bytes_per_update,
-                "kernel": "stencil3d_kernel<4>",
+                "algorithmic_bytes_per_launch": step_bytes * args.steps / max(k3_launches, 1),
+                "bytes_per_update": bytes_per_update,
+                "kernel": "stencil3d_kernel<4, 2> (its one-particle form <4, 1> runs the final "
+                          f"run: {final_updates / k3_updates_step:.2%} of the updates, at "
+                          f"{2 * C * 4 + 4} B per update)",
                 "plan": {"particles_per_item": plan_np, "tz": plan_tz,
                          "tile": "32x11 columns", "memberships": "float2 pair words"},
                 "kernel_ms": k3_ms, "kernel_launches": k3_launches,
@@ -881,6 +930,9 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same volume and particles, 1 generation x "
                          "3 iterations")
+    ap.add_argument("--small-particles", type=int, default=0,
+                    help="with --small: this many particles (a smaller capture), under the "
+                         "full run's plan (2 particles per item, whole-column items)")
     ap.add_argument("--small-kind", choices=("bf16", "grad"), default=None,
                     help="profiling case of the bf16 stencil or of the adjoint kernels")
     args = ap.parse_args()

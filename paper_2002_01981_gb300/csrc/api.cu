@@ -186,6 +186,7 @@ struct RunBufs {
   float* ub[kMaxVols];
   float* u0p[kMaxVols];
   float* gs[kMaxVols];          // 1/G per voxel (gsum_kernel), one plane per volume
+  const float* gs_of[kMaxVols]; // the volume gs holds 1/G of (the runs of one call reuse it)
   int pbase[kMaxVols];
   long long rec_base[kMaxVols];
   int rec_per_particle[kMaxVols];
@@ -431,6 +432,7 @@ struct BatchVol {
   double* fitness;        // device [P] or NULL
   int32_t* iters;         // device [P] or NULL
   double* c_out;          // device [P][c] or NULL
+  bool start_eq2 = false; // u0 comes from Eq 2 (the memberships of a voxel sum to one)
 };
 
 // ------------------------------------------------------- stencil plans
@@ -528,7 +530,11 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
   a.dmax = rb.dmax;
   a.n_records = rb.n_records;
   a.status = status;
-  a.sum_one = kind != 0;   // later iterations read Eq 2's memberships
+  // iterations after the first read Eq 2's memberships; the first reads the
+  // start, which may come from Eq 2 as well (pifcm3d's FCM start)
+  bool starts_eq2 = true;
+  for (int v = 0; v < n; ++v) starts_eq2 = starts_eq2 && vols[v].start_eq2;
+  a.sum_one = kind != 0 || starts_eq2;
   a.wait_ns = g_wait_ns.load();
   fill_method(a, p);
   for (int v = 0; v < n; ++v) {
@@ -731,8 +737,10 @@ struct BatchRun {
       if (rb->layout == UL_F32P)
         for (int v = 0; v < n; ++v) {
           const ifcm_shape& s = vols[v].shape;
-          if (s.nz > 1)
+          if (s.nz > 1 && rb->gs_of[v] != vols[v].x) {
             CU_TRY(launch_gsum(vols[v].x, s.nx, s.ny, s.nz, s.pitch_x, rb->gs[v], st));
+            rb->gs_of[v] = vols[v].x;
+          }
         }
       ST_TRY(choose_plan(vols, n, p, *rb, status, st, &pl));
       rb->np = pl.np;
@@ -832,11 +840,12 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
 }
 
 // The runs of P particles of one volume from the shared start (u0, c0).
+// start_eq2: u0 is a membership field from Eq 2 (e.g. the FCM start).
 ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* p,
                         const double* lam_xi, int P, const float* u0, const double* c0,
                         RunBufs& rb, double* fitness, int32_t* iters, double* c_out,
-                        DevStatus* status, cudaStream_t st) {
-  BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out};
+                        DevStatus* status, cudaStream_t st, bool start_eq2 = false) {
+  BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out, start_eq2};
   return run_stencil_batch(&bv, 1, p, rb, status, st);
 }
 
@@ -1534,7 +1543,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   CU_TRY(launch_pso_init(sw, st));
   if (o->fitness_mode == PIFCM_FITNESS_ONESTEP) {
     // each particle's (U, C) persists: generation g is iteration g of its run
-    BatchVol bv{xr, rs, P, sw.x, b.u0, b.c0, b.fitness, b.iters, nullptr};
+    BatchVol bv{xr, rs, P, sw.x, b.u0, b.c0, b.fitness, b.iters, nullptr, true};
     BatchRun br;
     ST_TRY(br.prepare(&bv, 1, p, rb, b.status, o->generations, 0.0, st));
     for (int g = 0; g < o->generations; ++g) {
@@ -1546,7 +1555,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
     for (int g = 0; g < o->generations; ++g) {
       const Trace tr("generation %d", g);
       ST_TRY(run_stencil(xr, rs, p, sw.x, P, b.u0, b.c0, rb, b.fitness, b.iters, nullptr,
-                         b.status, st));
+                         b.status, st, true));
       CU_TRY(launch_pso_step(sw, b.fitness, st));
     }
   }
@@ -1554,7 +1563,7 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   const Trace tr("final run");
   CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));
   ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
-                     b.c_final, b.status, st));
+                     b.c_final, b.status, st, true));
   if (u_out) ST_TRY(copy_out(rb, c, rpl, u_out, st));
   CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
                        b.iters_init, b.updates, b.best, b.status, result, st));

@@ -157,6 +157,45 @@ struct ReduceArgs {
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s);
 
+// ------------------------------------------- resident runs (resident.cu)
+// Whole runs of volumes small enough for shared memory: CTA gp runs particle
+// gp of the launch (volume v's particle p is gp = pbase_v + p) through every
+// iteration of its run with x, U^t and U^{t+1} held in shared memory.
+constexpr int kResidentThreads = 512;
+constexpr size_t kResidentSmemBytes = 225 * 1024;     // dynamic shared memory, at most
+
+struct ResidentVol {
+  const float* x;               // normalised volume [nz][ny][pitch]
+  const float* u0;              // shared start [c][nz][ny][pitch], or NULL for u = 1/c
+  const double* c0;             // [c] C^0, or NULL for c_j = (j + 1/2) / c
+  const double* lam_xi;         // [P][2], or NULL for lambda = xi = 0
+  double* fitness;              // [P] J of the last iteration, or NULL
+  int32_t* iters_out;           // [P] iterations executed, or NULL
+  double* c_out;                // [P][c] final centres, or NULL
+  float* u_final;               // [c][nz][ny][pitch] final U of particle 0, or NULL
+  int nx, ny, nz, pitch;
+  int P, pbase;
+};
+
+struct ResidentArgs {
+  ResidentVol vol[kMaxVols];
+  int n_vol;
+  RunState st;                  // [particles of the launch]: written at the end of each run
+  float dist_floor, m, inv_m1;
+  int m_is_2;
+  int max_iter;
+  double eps;
+  int reduce;                   // IFCM_REDUCE_FP64 or IFCM_REDUCE_COMP32 across warps
+  int stencil;                  // 0: no neighbourhood terms (the FCM start)
+  DevStatus* status;
+};
+
+// Dynamic shared memory of a resident run: x plus two membership fields.
+size_t resident_smem_bytes(int c, long long nvox);
+// One launch of P_total CTAs; max_nvox = the largest volume of the launch.
+cudaError_t launch_resident(int c, const ResidentArgs& a, int P_total, long long max_nvox,
+                            cudaStream_t s);
+
 // ------------------------------------------------ reverse pass (adjoint.cu)
 // One iteration t of the reverse pass over K unrolled IFCM iterations.
 struct AdjointArgs {
