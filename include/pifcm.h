@@ -226,6 +226,20 @@ void ifcm_autotune_reset(void);
  * (clamped so that chunks keep >= 8 planes).  np = 0 lifts it.  For tests
  * and experiments.  IFCM_ERR_INVALID for np outside 0..2 or chunks < 1. */
 ifcm_status ifcm_stencil_force_plan(int32_t np, int32_t chunks);
+/* Whole runs of small volumes in one launch (Alg 1 step 4 with Alg 2's loop
+ * of steps 6-10 on the device).  When every volume of a batch fits one CTA's
+ * shared memory -- x and two FP32 membership fields, (1 + 2c) x 4 bytes per
+ * voxel, at most 225 KB (6400 voxels at c = 4, 3388 at c = 8) -- and the
+ * batch stores FP32 memberships with V = 1, it runs as one launch of one CTA
+ * per particle: the CTA keeps x, U^t and U^{t+1} in shared memory, sums
+ * Eqs 1 and 3 (FP32 within a warp, FP64 or compensated FP32 across warps, as
+ * `reduce` says) and takes the stop rule itself, instead of two launches per
+ * iteration.  pifcm3d's FCM start (Alg 1 step 2) runs the same way.  The
+ * arithmetic per voxel is the plain kernel's; results agree with the stencil
+ * form up to FP32 rounding.  Mode 1 (default): on; 0: off, every batch takes
+ * the stencil kernels.  A forced plan (ifcm_stencil_force_plan) also keeps
+ * batches on the stencil kernels.  Process-wide. */
+void ifcm_resident_enable(int32_t mode);
 /* The plan a one-volume batch of P particles would use: *np, *tz.  Returns 1
  * when it comes from the tuning cache, 0 from the rule, -1 on bad input. */
 int32_t ifcm_stencil_plan(ifcm_shape shape, int32_t c, int32_t P, int32_t* np, int32_t* tz);

@@ -518,6 +518,8 @@ std::vector<long long> plan_key(const BatchVol* vols, int n, int c, int u_dtype)
 // writes ua, 1 reads ua and writes ub, 2 reads ub and writes ua.
 // Bound of every mbarrier wait of the stencil kernels (ifcm_set_wait_limit_ns).
 std::atomic<unsigned long long> g_wait_ns{0};
+// Whole runs of small volumes in one launch (ifcm_resident_enable): on by default.
+std::atomic<int> g_resident{1};
 
 ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_params* p,
                        const RunBufs& rb, const StencilPlan& pl, int kind, DevStatus* status) {
@@ -734,7 +736,7 @@ struct BatchRun {
     }
     if (!wide) {
       // 1/G of each 3D volume for the float2-pair kernel (plans are timed on it)
-      if (rb->layout == UL_F32P)
+      if (rb->layout == UL_F32P || rb->layout == UL_BF16)
         for (int v = 0; v < n; ++v) {
           const ifcm_shape& s = vols[v].shape;
           if (s.nz > 1 && rb->gs_of[v] != vols[v].x) {
@@ -829,10 +831,82 @@ struct BatchRun {
   }
 };
 
+// A batch whose every volume fits one CTA's shared memory (x, U^t and U^{t+1}),
+// with FP32 memberships and the first neighbourhood shell, runs whole: one
+// launch of one CTA per particle instead of two launches per iteration.
+bool resident_eligible(const BatchVol* vols, int n, const ifcm_params* p) {
+  if (!g_resident.load() || forced_np() > 0 || p->V != 1 || p->u_dtype != IFCM_U_FP32)
+    return false;
+  for (int v = 0; v < n; ++v) {
+    const ifcm_shape& s = vols[v].shape;
+    const long long nvox = static_cast<long long>(s.nx) * s.ny * s.nz;
+    if (resident_smem_bytes(p->c, nvox) > kResidentSmemBytes) return false;
+  }
+  return true;
+}
+
+// The resident form of a batch (resident.cu): every particle's run (Alg 1
+// step 4, reading R5) inside one launch; u_final (or NULL) receives particle
+// 0's final memberships of volume 0 as FP32 [c][plane].
+// stencil = false, max_iter >= 0: the FCM start instead (lambda = xi = 0, no
+// neighbourhood terms, max_iter iterations at most).
+ifcm_status run_resident(const BatchVol* vols, int n, const ifcm_params* p, RunBufs& rb,
+                         DevStatus* status, float* u_final, cudaStream_t st,
+                         bool stencil = true, int max_iter = -1) {
+  const Trace tr("resident runs");
+  ResidentArgs a{};
+  a.n_vol = n;
+  a.st = rb.st;
+  a.dist_floor = static_cast<float>(p->dist_floor);
+  a.m = static_cast<float>(p->m);
+  a.inv_m1 = static_cast<float>(1.0 / (p->m - 1.0));
+  a.m_is_2 = p->m == 2.0;
+  a.max_iter = max_iter >= 0 ? max_iter : p->max_iter;
+  a.eps = p->eps_u;
+  a.reduce = p->reduce;
+  a.stencil = stencil ? 1 : 0;
+  a.status = status;
+  int P_total = 0;
+  long long max_nvox = 0;
+  for (int v = 0; v < n; ++v) {
+    const BatchVol& bv = vols[v];
+    ResidentVol& rv = a.vol[v];
+    rv.x = bv.x;
+    rv.u0 = bv.u0;
+    rv.c0 = bv.c0;
+    rv.lam_xi = bv.lam_xi;
+    rv.fitness = bv.fitness;
+    rv.iters_out = bv.iters;
+    rv.c_out = bv.c_out;
+    rv.u_final = v == 0 ? u_final : nullptr;
+    rv.nx = bv.shape.nx;
+    rv.ny = bv.shape.ny;
+    rv.nz = bv.shape.nz;
+    rv.pitch = bv.shape.pitch_x;
+    rv.P = bv.P;
+    rv.pbase = P_total;
+    P_total += bv.P;
+    const long long nvox = static_cast<long long>(bv.shape.nx) * bv.shape.ny * bv.shape.nz;
+    if (nvox > max_nvox) max_nvox = nvox;
+  }
+  CU_TRY(launch_resident(p->c, a, P_total, max_nvox, st));
+  return IFCM_OK;
+}
+
 // IFCM runs of every particle of n volumes with the stencil kernel (the plain
 // kernel for V > 1): one launch per iteration covers all volumes' work items.
+// Batches of small volumes run resident instead (resident_eligible); then,
+// when u_final is given, particle 0's final memberships of volume 0 go there
+// and *u_written is set.
 ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p, RunBufs& rb,
-                              DevStatus* status, cudaStream_t st) {
+                              DevStatus* status, cudaStream_t st, float* u_final = nullptr,
+                              bool* u_written = nullptr) {
+  if (u_written) *u_written = false;
+  if (resident_eligible(vols, n, p)) {
+    ST_TRY(run_resident(vols, n, p, rb, status, u_final, st));
+    if (u_written) *u_written = u_final != nullptr;
+    return IFCM_OK;
+  }
   BatchRun br;
   ST_TRY(br.prepare(vols, n, p, rb, status, p->max_iter, p->eps_u, st));
   for (int it = 0; it < p->max_iter; ++it) ST_TRY(br.iteration(it, st));
@@ -844,9 +918,10 @@ ifcm_status run_stencil_batch(const BatchVol* vols, int n, const ifcm_params* p,
 ifcm_status run_stencil(const float* x, const ifcm_shape& s, const ifcm_params* p,
                         const double* lam_xi, int P, const float* u0, const double* c0,
                         RunBufs& rb, double* fitness, int32_t* iters, double* c_out,
-                        DevStatus* status, cudaStream_t st, bool start_eq2 = false) {
+                        DevStatus* status, cudaStream_t st, bool start_eq2 = false,
+                        float* u_final = nullptr, bool* u_written = nullptr) {
   BatchVol bv{x, s, P, lam_xi, u0, c0, fitness, iters, c_out, start_eq2};
-  return run_stencil_batch(&bv, 1, p, rb, status, st);
+  return run_stencil_batch(&bv, 1, p, rb, status, st, u_final, u_written);
 }
 
 // Method constants of a plain-kernel launch, and the shells with their Eq 10
@@ -1122,9 +1197,10 @@ ifcm_status ifcm_fit(const float* x, ifcm_shape shape, const ifcm_params* p,
     CU_TRY(launch_fill(uni, 1.0f / p->c, static_cast<long long>(p->c) * plane_elems(shape), st));
     start = uni;
   }
+  bool written = false;
   ST_TRY(run_stencil(x, shape, p, lam_xi, 1, start, c_init, rb, J_out, iters_out, c_out, status,
-                     st));
-  if (u_out) ST_TRY(copy_out(rb, p->c, plane_elems(shape), u_out, st));
+                     st, false, u_out, &written));
+  if (u_out && !written) ST_TRY(copy_out(rb, p->c, plane_elems(shape), u_out, st));
   return IFCM_OK;
 }
 
@@ -1520,14 +1596,21 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
 
   RunBufs rb = b.run;
   rb.st.updates = b.updates;
-  // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c.
+  // Algorithm 1 step 2: FCM start (lambda = xi = 0) from u = 1/c, c_j = (j+1/2)/c;
+  // one resident launch when the (sliced) volume fits a CTA's shared memory.
   {
     const Trace tr("fcm start");
-    ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr, o->init_max_iter,
-                     rb, b.iters_init, b.c0, b.J_init, b.status, false, st));
+    const long long nvox = static_cast<long long>(rs.nx) * rs.ny * rs.nz;
+    if (g_resident.load() && resident_smem_bytes(c, nvox) <= kResidentSmemBytes) {
+      BatchVol sv{xr, rs, 1, nullptr, nullptr, nullptr, b.J_init, b.iters_init, b.c0};
+      ST_TRY(run_resident(&sv, 1, p, rb, b.status, b.u0, st, false, o->init_max_iter));
+    } else {
+      ST_TRY(run_plain(xr, rs, p, nullptr, 0.0f, 0.0f, false, nullptr, nullptr,
+                       o->init_max_iter, rb, b.iters_init, b.c0, b.J_init, b.status, false, st));
+      CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0,
+                                static_cast<long long>(c) * rpl, st));
+    }
   }
-  CU_TRY(launch_select_copy(rb.ua[0], rb.ub[0], rb.st.iters, b.u0,
-                            static_cast<long long>(c) * rpl, st));
 
   // Algorithm 1 steps 3-9.
   pso_state sw{};
@@ -1562,9 +1645,10 @@ ifcm_status pifcm3d(const float* vol, ifcm_shape shape, const ifcm_params* p,
   // Algorithm 1 step 11: final IFCM at the best personal best.
   const Trace tr("final run");
   CU_TRY(launch_pso_best(sw.pbest_x, sw.pbest_f, P, b.lam_best, b.best, st));
+  bool written = false;
   ST_TRY(run_stencil(xr, rs, p, b.lam_best, 1, b.u0, b.c0, rb, b.J_final, b.iters_final,
-                     b.c_final, b.status, st, true));
-  if (u_out) ST_TRY(copy_out(rb, c, rpl, u_out, st));
+                     b.c_final, b.status, st, true, u_out, &written));
+  if (u_out && !written) ST_TRY(copy_out(rb, c, rpl, u_out, st));
   CU_TRY(launch_result(c, b.c_final, b.lam_best, b.J_final, sw.pbest_f, P, b.iters_final,
                        b.iters_init, b.updates, b.best, b.status, result, st));
   return IFCM_OK;
@@ -1626,6 +1710,8 @@ ifcm_status pifcm3d_host(const float* vol_host, ifcm_shape shape, const ifcm_par
 }
 
 void ifcm_set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns); }
+
+void ifcm_resident_enable(int32_t mode) { g_resident.store(mode ? 1 : 0); }
 
 // ------------------------------------------------------------ profiling
 void ifcm_profile_enable(int32_t on) {

@@ -1,9 +1,22 @@
 // The stencil kernel over bf16 pair words with one particle per work item
 // (every c): word (particle p, pair k) holds clusters 2k and 2k+1 of p, the
 // two lanes of the packed FP32x2 sums.
-#include "stencil_kernel.cuh"
+#include "stencil3d.cuh"
 
 namespace pifcm {
+
+namespace {
+template <int C>
+cudaError_t launch_np1_bf16(const StencilArgs& a, int grid, cudaStream_t s) {
+  bool deep = false;
+  for (int v = 0; v < a.n_vol; ++v)
+    deep = deep || stencil3d_eligible(UL_BF16, 1, a.m_is_2, a.sum_one, a.vol[v].nz);
+  if (!deep) return launch_c<C, 1, UL_BF16>(a, grid, s);
+  cudaError_t e = launch3d_c<C, 1, UL_BF16>(a, grid, s);
+  if (e != cudaSuccess) return e;
+  return launch_c<C, 1, UL_BF16>(a, grid, s, false);    // the 2D images of the batch
+}
+}  // namespace
 
 size_t smem_bytes_bf16_np1(int c) {
   switch (c) {
@@ -31,13 +44,13 @@ int blocks_per_sm_bf16_np1(int c) {
 
 cudaError_t launch_stencil_bf16_np1(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, 1, UL_BF16>(a, grid, s);
-    case 3: return launch_c<3, 1, UL_BF16>(a, grid, s);
-    case 4: return launch_c<4, 1, UL_BF16>(a, grid, s);
-    case 5: return launch_c<5, 1, UL_BF16>(a, grid, s);
-    case 6: return launch_c<6, 1, UL_BF16>(a, grid, s);
-    case 7: return launch_c<7, 1, UL_BF16>(a, grid, s);
-    case 8: return launch_c<8, 1, UL_BF16>(a, grid, s);
+    case 2: return launch_np1_bf16<2>(a, grid, s);
+    case 3: return launch_np1_bf16<3>(a, grid, s);
+    case 4: return launch_np1_bf16<4>(a, grid, s);
+    case 5: return launch_np1_bf16<5>(a, grid, s);
+    case 6: return launch_np1_bf16<6>(a, grid, s);
+    case 7: return launch_np1_bf16<7>(a, grid, s);
+    case 8: return launch_np1_bf16<8>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,9 +1,22 @@
 // The stencil kernel over bf16 pair words with two particles per work item
 // (c <= 5): word (pair k, cluster j) holds cluster j of particles 2k and
 // 2k+1, the two lanes of the packed FP32x2 sums.
-#include "stencil_kernel.cuh"
+#include "stencil3d.cuh"
 
 namespace pifcm {
+
+namespace {
+template <int C>
+cudaError_t launch_np2_bf16(const StencilArgs& a, int grid, cudaStream_t s) {
+  bool deep = false;
+  for (int v = 0; v < a.n_vol; ++v)
+    deep = deep || stencil3d_eligible(UL_BF16, 2, a.m_is_2, a.sum_one, a.vol[v].nz);
+  if (!deep) return launch_c<C, 2, UL_BF16>(a, grid, s);
+  cudaError_t e = launch3d_c<C, 2, UL_BF16>(a, grid, s);
+  if (e != cudaSuccess) return e;
+  return launch_c<C, 2, UL_BF16>(a, grid, s, false);    // the 2D images of the batch
+}
+}  // namespace
 
 size_t smem_bytes_bf16_np2(int c) {
   switch (c) {
@@ -25,10 +38,10 @@ int blocks_per_sm_bf16_np2(int c) {
 
 cudaError_t launch_stencil_bf16_np2(int c, const StencilArgs& a, int grid, cudaStream_t s) {
   switch (c) {
-    case 2: return launch_c<2, 2, UL_BF16>(a, grid, s);
-    case 3: return launch_c<3, 2, UL_BF16>(a, grid, s);
-    case 4: return launch_c<4, 2, UL_BF16>(a, grid, s);
-    case 5: return launch_c<5, 2, UL_BF16>(a, grid, s);
+    case 2: return launch_np2_bf16<2>(a, grid, s);
+    case 3: return launch_np2_bf16<3>(a, grid, s);
+    case 4: return launch_np2_bf16<4>(a, grid, s);
+    case 5: return launch_np2_bf16<5>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

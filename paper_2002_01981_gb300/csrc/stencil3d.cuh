@@ -58,25 +58,40 @@ constexpr int SBYTES = ((TX * TY * 4 + 127) / 128) * 128;   // 1/G of the tile's
 
 // Pair words per voxel (K), H sums kept (KH), and whether the last cluster's H
 // is taken by complement (COMPL) and the last word's high lane is padding (PAD).
-template <int C, int NP>
+// With bf16 words the memberships of a voxel sum to one only up to their
+// rounding, so no cluster's H is taken by complement there.
+template <int C, int NP, int UL>
 struct S3 {
   static constexpr int K = Pairs<C, NP>::K;
   static constexpr bool PAD = NP == 1 && (C & 1);
-  static constexpr bool COMPL = NP == 2 || PAD;
+  static constexpr bool COMPL = UL == UL_F32P && (NP == 2 || PAD);
   static constexpr int KH = COMPL ? K - 1 : K;
 };
 
-template <int C, int NP>
+// A pair word in a stage: float2, or a bf16 pair unpacked exactly.
+template <int UL>
+struct Word3 {
+  using T = float2;
+  static __device__ __forceinline__ float2 get(const T* p, int i) { return p[i]; }
+};
+template <>
+struct Word3<UL_BF16> {
+  using T = uint32_t;
+  static __device__ __forceinline__ float2 get(const T* p, int i) { return unpack_bf16x2(p[i]); }
+};
+
+template <int C, int NP, int UL>
 __host__ __device__ constexpr int s3_stage_bytes() {
-  return XBYTES + SBYTES + ublock_bytes<C, NP, UL_F32P>();
+  return XBYTES + SBYTES + ublock_bytes<C, NP, UL>();
 }
-template <int C, int NP>
+template <int C, int NP, int UL>
 __host__ __device__ constexpr uint32_t s3_tx_bytes() {
-  return static_cast<uint32_t>(PLANE * 4 + TX * TY * 4 + S3<C, NP>::K * PLANE * 8);
+  return static_cast<uint32_t>(PLANE * 4 + TX * TY * 4 +
+                               S3<C, NP, UL>::K * PLANE * word_bytes(UL));
 }
-template <int C, int NP>
+template <int C, int NP, int UL>
 __host__ __device__ constexpr int s3_smem_total() {
-  return NSTAGE * s3_stage_bytes<C, NP>() + 128;
+  return NSTAGE * s3_stage_bytes<C, NP, UL>() + 128;
 }
 static_assert(NSTAGE == 8, "stage indices are taken modulo 8 with a mask");
 static_assert(SBYTES % 128 == 0, "TMA destinations start on 128-byte boundaries");
@@ -88,9 +103,9 @@ static_assert(BX + 4 - BX - 1 >= 0 && TY * BX + TX - 1 + 4 + BX + 1 < PLANE,
 
 // One centre of the column: its sums over the planes read so far, one float2
 // per pair word.
-template <int C, int NP>
+template <int C, int NP, int UL>
 struct Slot3 {
-  static constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
+  static constexpr int K = S3<C, NP, UL>::K, KH = S3<C, NP, UL>::KH;
   float2 H[KH];                      // sum_k u_kj g_ik (the last cluster's by complement)
   float2 F[K];                       // sum_k u_kj^2 q^2_ik
   float x;                           // x_i
@@ -106,18 +121,18 @@ struct Slot3 {
 };
 
 // Constants of an item, paired like the sums.
-template <int C, int NP>
+template <int C, int NP, int UL>
 struct Fin3 {
-  float2 ncc[S3<C, NP>::K];          // -c_j, paired like the sums (0 in a padding lane)
+  float2 ncc[S3<C, NP, UL>::K];          // -c_j, paired like the sums (0 in a padding lane)
   float2 nlam, nxi;                  // -lambda, -xi of the lanes' particles
   float floor;                       // dist_floor
 };
 
 // A thread's shares of the item's sums; with one particle, J and max|du| are
 // in the low lane.
-template <int C, int NP>
+template <int C, int NP, int UL>
 struct Acc3 {
-  static constexpr int K = S3<C, NP>::K;
+  static constexpr int K = S3<C, NP, UL>::K;
   float2 s0[K], s1[K];               // sum u^m, sum u^m x
   float2 J, dm;                      // J, max|du|
   __device__ __forceinline__ void clear() {
@@ -131,12 +146,15 @@ struct Acc3 {
 // 1/Q from invq, the last cluster's H by complement), Eq 4 with reading R2,
 // Eq 2 for m = 2, the U^{t+1} store and the centre's shares of Eqs 1 and 3
 // and of max|du|.  ud: the centre's U^t in its stage (pair words at its
-// column); dst: its U^{t+1} word of pair 0.
-template <int C, int NP>
-__device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __restrict__ ud,
-                                     float invq, const Fin3<C, NP>& fc, Acc3<C, NP>& acc,
-                                     float2* __restrict__ dst, int plane, bool st) {
-  constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
+// column); dst: its U^{t+1} word of pair 0.  With bf16 words U^{t+1} is
+// rounded to nearest even when stored and max|du| compares stored values;
+// Eqs 1 and 3 take the FP32 u' that was rounded.
+template <int C, int NP, int UL>
+__device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
+                                     const typename Word3<UL>::T* __restrict__ ud, float invq,
+                                     const Fin3<C, NP, UL>& fc, Acc3<C, NP, UL>& acc,
+                                     typename Word3<UL>::T* __restrict__ dst, int plane, bool st) {
+  constexpr int K = S3<C, NP, UL>::K, KH = S3<C, NP, UL>::KH;
   const float ig = fabsf(d.s);
   // f_j = 1 - lambda H_j - xi F_j with H_j = Hs_j / G and F_j = Fs_j / Q,
   // taking -lambda / G and -xi / Q once per centre
@@ -144,7 +162,7 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __rest
   float2 fq[K];
 #pragma unroll
   for (int q = 0; q < KH; ++q) fq[q] = __ffma2_rn(nx, d.F[q], __ffma2_rn(nl, d.H[q], dup2(1.0f)));
-  if (S3<C, NP>::COMPL) {
+  if (S3<C, NP, UL>::COMPL) {
     // the last cluster: 1 - lambda (1 - sum_{j<c-1} H_j) - xi F, with the
     // other clusters' sums of its particle (per lane for NP = 2; both lanes
     // of every other word for NP = 1, whose last word's high lane is padding)
@@ -163,7 +181,7 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __rest
     const float2 d2 = max2(__fmul2_rn(__fmul2_rn(dd, dd), fq[q]), fc.floor);
     r[q] = make_float2(fast_rcp(d2.x), fast_rcp(d2.y));
   }
-  if (S3<C, NP>::PAD) r[K - 1].y = 0.0f;     // the padding lane is no cluster
+  if (S3<C, NP, UL>::PAD) r[K - 1].y = 0.0f;     // the padding lane is no cluster
   // Eq 2 with m = 2: u_j = (1/d2_j) / S, S = sum_k 1/d2_k; Eq 1 share = 1/S
   float2 S = r[0];
 #pragma unroll
@@ -183,8 +201,15 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __rest
     const float2 um = __fmul2_rn(u, u);
     acc.s0[q] = __fadd2_rn(acc.s0[q], um);
     acc.s1[q] = __ffma2_rn(um, x2, acc.s1[q]);
-    if (st) __stcg(&dst[q * plane], u);
-    const float2 e = __ffma2_rn(ud[q * PLANE], dup2(-1.0f), u);   // u' - u
+    float2 e;                                                      // u' - u
+    if constexpr (UL == UL_BF16) {
+      const uint32_t w = pack_bf16x2(u);
+      if (st) __stcg(reinterpret_cast<unsigned int*>(&dst[q * plane]), w);
+      e = __ffma2_rn(unpack_bf16x2(ud[q * PLANE]), dup2(-1.0f), unpack_bf16x2(w));
+    } else {
+      if (st) __stcg(&dst[q * plane], u);
+      e = __ffma2_rn(ud[q * PLANE], dup2(-1.0f), u);
+    }
     if (NP == 2) {
       acc.dm.x = fmaxf(acc.dm.x, fabsf(e.x));
       acc.dm.y = fmaxf(acc.dm.y, fabsf(e.y));
@@ -198,18 +223,21 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP>& d, const float2* __rest
 // plane pz to centres pz - 1 (l), pz (m) and pz + 1 (h, whose sums start
 // here; its x and s come from stage pz + 1).  xs / us: stage pz at the
 // column; xn / sn: stage pz + 1 at the column; ud: stage pz - 2 at the column.
-template <int C, int NP, bool FIN>
-__device__ __forceinline__ void step3(const float* __restrict__ xs, const float2* __restrict__ us,
+template <int C, int NP, int UL, bool FIN>
+__device__ __forceinline__ void step3(const float* __restrict__ xs,
+                                      const typename Word3<UL>::T* __restrict__ us,
                                       const float* __restrict__ xn, const float* __restrict__ sn,
-                                      const float2* __restrict__ ud, Slot3<C, NP>& d,
-                                      Slot3<C, NP>& l, Slot3<C, NP>& m, Slot3<C, NP>& h,
-                                      float invq, const Fin3<C, NP>& fc, Acc3<C, NP>& acc,
-                                      float2* __restrict__ dst, int plane, bool st) {
-  constexpr int K = S3<C, NP>::K, KH = S3<C, NP>::KH;
+                                      const typename Word3<UL>::T* __restrict__ ud,
+                                      Slot3<C, NP, UL>& d, Slot3<C, NP, UL>& l,
+                                      Slot3<C, NP, UL>& m, Slot3<C, NP, UL>& h, float invq,
+                                      const Fin3<C, NP, UL>& fc, Acc3<C, NP, UL>& acc,
+                                      typename Word3<UL>::T* __restrict__ dst, int plane,
+                                      bool st) {
+  constexpr int K = S3<C, NP, UL>::K, KH = S3<C, NP, UL>::KH;
   h.x = xn[0];
   h.s = sn[0];
   h.xg = h.s < 0.0f ? h.x + 2.0f : h.x;
-  if (FIN) fin3<C, NP>(d, ud, invq, fc, acc, dst, plane, st);
+  if (FIN) fin3<C, NP, UL>(d, ud, invq, fc, acc, dst, plane, st);
   float2 W0[K], S1[K], S2[K];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
@@ -226,7 +254,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
       const float gm = self ? 0.0f : fabsf(m.xg - xk);
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        const float2 uk = us[q * PLANE + off];
+        const float2 uk = Word3<UL>::get(us, q * PLANE + off);
         if (q < KH) {
           l.H[q] = __ffma2_rn(uk, dup2(gl), l.H[q]);
           h.H[q] = first ? __fmul2_rn(uk, dup2(gh)) : __ffma2_rn(uk, dup2(gh), h.H[q]);
@@ -248,9 +276,10 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs, const float2
   }
 }
 
-template <int C, int NP>
+template <int C, int NP, int UL>
 __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant__ StencilArgs a) {
-  constexpr int K = S3<C, NP>::K;
+  constexpr int K = S3<C, NP, UL>::K;
+  using WT = typename Word3<UL>::T;
   extern __shared__ unsigned char dsmem_raw[];
   __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ uint32_t lastq[NSTAGE];    // the last plane loaded into each stage
@@ -265,7 +294,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   unsigned char* dsmem = dsmem_raw + ((128u - (smem_addr(dsmem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  constexpr int SB = s3_stage_bytes<C, NP>();
+  constexpr int SB = s3_stage_bytes<C, NP, UL>();
   const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   // Active units of every volume (pairs (2k, 2k+1) active while either runs,
@@ -323,7 +352,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       return;
     unsigned char* st = dsmem + s * SB;
     lastq[s] = qq;
-    mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C, NP>());
+    mbar_arrive_expect_tx(&full[s], s3_tx_bytes<C, NP, UL>());
     tma_load_3d(st, &a.tm_x[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz);
     tma_load_3d(st + XBYTES, &a.tm_s[it.v], &full[s], it.x0, it.y0, pz);
     tma_load_4d(st + XBYTES + SBYTES, &a.tm_u[it.v], &full[s], it.x0 - 4, it.y0 - 1, pz,
@@ -337,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       uint32_t q = 0;
       bool go = true;
       for (int w = blockIdx.x; go && w < n_items; w += gridDim.x) {
-        const Item it = decode_item<NP, UL_F32P>(a, tab, w);
+        const Item it = decode_item<NP, UL>(a, tab, w);
         for (int pz = it.pzb; pz <= it.pze; ++pz, ++q) {
           const uint32_t s = q & (NSTAGE - 1);
           if (q >= NSTAGE && !mbar_wait_bounded(&empty[s], ((q / NSTAGE) - 1) & 1, wait_ns)) {
@@ -354,7 +383,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
         }
       }
     }
-  }
+  } else {
 
   // ------------------------------------------------------------ consumers
   const int tx = tid & 31, ty = tid >> 5;
@@ -369,8 +398,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
     return reinterpret_cast<const float*>(dsmem + (qq & (NSTAGE - 1)) * SB + XBYTES) + sidx;
   };
   auto us_at = [&](uint32_t qq) {
-    return reinterpret_cast<const float2*>(dsmem + (qq & (NSTAGE - 1)) * SB + XBYTES + SBYTES) +
-           cidx;
+    return reinterpret_cast<const WT*>(dsmem + (qq & (NSTAGE - 1)) * SB + XBYTES + SBYTES) + cidx;
   };
   auto wait_full = [&](uint32_t qq) -> bool {
     if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
@@ -389,8 +417,8 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
     if (lane == 0) mbar_arrive(&empty[qq & (NSTAGE - 1)]);
   };
 
-  for (int w = blockIdx.x; warp < NCW && w < n_items; w += gridDim.x) {
-    const Item it = decode_item<NP, UL_F32P>(a, tab, w);
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const Item it = decode_item<NP, UL>(a, tab, w);
     const VolDesc& vd = a.vol[it.v];
     const uint32_t q0 = q;
     const int plane = vd.nz * vd.ny * vd.pitch;
@@ -407,16 +435,17 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
         for (int j = 0; j < C; ++j)
           cc[p][j] = static_cast<float>(a.centres[(vd.pbase + pid) * C + j]);
       }
-      s_ic.dst[0] = vd.u_dst + static_cast<size_t>(it.unit) * K * plane * 2;
+      s_ic.dst[0] = vd.u_dst + static_cast<size_t>(it.unit) * K * plane * (word_bytes(UL) / 4);
       s_ic.nlam = make_float2(-lam[0], -lam[1]);
       s_ic.nxi = make_float2(-xi[0], -xi[1]);
 #pragma unroll
       for (int q = 0; q < K; ++q)
         s_ic.ncc[q] = NP == 2 ? make_float2(-cc[0][q], -cc[1][q])
-                              : make_float2(-cc[0][2 * q], 2 * q + 1 < C ? -cc[0][2 * q + 1] : 0.0f);
+                              : make_float2(-cc[0][2 * q],
+                                            2 * q + 1 < C ? -cc[0][2 * q + 1] : 0.0f);
     }
     consumer_sync();
-    Acc3<C, NP> acc;
+    Acc3<C, NP, UL> acc;
     acc.clear();
 
     {
@@ -427,7 +456,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
         box_counts(cx.X, cx.Y, 0, vd.nx, vd.ny, vd.nz, cnt, Q);
         iqz = cnt > 0 ? __frcp_rn(Q) : 0.0f;
       }
-      Fin3<C, NP> fc;
+      Fin3<C, NP, UL> fc;
 #pragma unroll
       for (int q = 0; q < K; ++q) fc.ncc[q] = s_ic.ncc[q];
       fc.nlam = s_ic.nlam;
@@ -435,15 +464,15 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       fc.floor = a.dist_floor;
       const float iqc = cx.invQ_col;
       // stores of the column (the item's centres lie in [z0, z1) of the volume)
-      const bool st = cx.col_ok &&
-                      IFCM_CHECK(it.z0 >= 0 && it.z1 <= vd.nz &&
-                                     (static_cast<long long>(it.unit) + 1) * K * plane * 2 <=
-                                         vd.dst_elems,
-                                 a.status, 32);
-      float2* const col_dst = reinterpret_cast<float2*>(s_ic.dst[0]) + cx.col_off;
+      const long long unit_end =
+          (static_cast<long long>(it.unit) + 1) * K * plane * (word_bytes(UL) / 4);
+      const bool st = cx.col_ok && IFCM_CHECK(it.z0 >= 0 && it.z1 <= vd.nz &&
+                                                  unit_end <= vd.dst_elems,
+                                              a.status, 32);
+      WT* const col_dst = reinterpret_cast<WT*>(s_ic.dst[0]) + cx.col_off;
       const int zstride = vd.ny * vd.pitch;
 
-      Slot3<C, NP> s0, s1, s2, s3;
+      Slot3<C, NP, UL> s0, s1, s2, s3;
       // the first step whose delayed finalisation is a centre of the item
       const int kf = it.z0 - it.pzb + 2;
       // the generic step covers the steps before the first interior-z centre
@@ -470,13 +499,13 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
         const int zd = it.pzb + kk - 2;
         if (ok) {
           const float invq = zd == 0 ? iqz : iqc;
-          float2* dst = col_dst + static_cast<long long>(zd) * zstride;
+          WT* dst = col_dst + static_cast<long long>(zd) * zstride;
           if (kk >= kf)
-            step3<C, NP, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6), s0,
-                           s1, s2, s3, invq, fc, acc, dst, plane, st);
+            step3<C, NP, UL, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1),
+                                   us_at(qq + 6), s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
           else
-            step3<C, NP, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1), us_at(qq + 6),
-                            s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
+            step3<C, NP, UL, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1),
+                                    us_at(qq + 6), s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
         }
         if (!landed2) ok = ok && wait_full(qq + 2);
         if (kk >= 2) release(qq - 2);
@@ -491,18 +520,19 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       // step has its finalisation, an interior-z centre, and two stages ahead
       for (; ok && kk + 4 <= np - 2; kk += 4) {
         const uint32_t qq = q0 + kk;
-        float2* dst = col_dst + static_cast<long long>(it.pzb + kk - 2) * zstride;
+        WT* dst = col_dst + static_cast<long long>(it.pzb + kk - 2) * zstride;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const uint32_t qr = qq + r;
           const bool landed2 =
               mbar_test_wait(&full[(qr + 2) & (NSTAGE - 1)], ((qr + 2) / NSTAGE) & 1);
-          Slot3<C, NP>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
-          Slot3<C, NP>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
-          Slot3<C, NP>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
-          Slot3<C, NP>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
-          step3<C, NP, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1), us_at(qr + 6), d, l,
-                         m, h, iqc, fc, acc, dst + r * zstride, plane, st);
+          Slot3<C, NP, UL>& d = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
+          Slot3<C, NP, UL>& l = r == 0 ? s1 : r == 1 ? s2 : r == 2 ? s3 : s0;
+          Slot3<C, NP, UL>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
+          Slot3<C, NP, UL>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
+          step3<C, NP, UL, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1),
+                                 us_at(qr + 6), d, l, m, h, iqc, fc, acc, dst + r * zstride, plane,
+                                 st);
           if (!landed2) ok = ok && wait_full(qr + 2);
           release(qr - 2);
         }
@@ -515,11 +545,11 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       const bool live = ok && !*reinterpret_cast<volatile int*>(&s_abort);
       const int zl = it.pze - 1;
       if (live && np >= 2 && zl >= it.z0 && zl < it.z1)
-        fin3<C, NP>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
-                col_dst + static_cast<long long>(zl) * zstride, plane, st);
+        fin3<C, NP, UL>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
+                        col_dst + static_cast<long long>(zl) * zstride, plane, st);
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1)
-        fin3<C, NP>(s1, us_at(ql), iqz, fc, acc, col_dst + static_cast<long long>(it.pze) * zstride,
-                plane, st);
+        fin3<C, NP, UL>(s1, us_at(ql), iqz, fc, acc,
+                        col_dst + static_cast<long long>(it.pze) * zstride, plane, st);
       if (np >= 2) release(ql - 1);
       release(ql);
     }
@@ -578,6 +608,8 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
     consumer_sync();
   }
 
+  }   // consumers
+
   // After a timeout the consumers skipped their waits: before the CTA exits,
   // wait (bounded) for the copies still landing in its shared memory.  No
   // load is issued after the abort, so each stage has at most one.
@@ -588,14 +620,14 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   }
 }
 
-// One launch of the 3D float2-pair kernel (it takes the 3D volumes of `a`).
-template <int C, int NP>
+// One launch of the 3D pair-word kernel (it takes the 3D volumes of `a`).
+template <int C, int NP, int UL = UL_F32P>
 cudaError_t launch3d_c(const StencilArgs& a, int grid, cudaStream_t s) {
-  constexpr int smem = s3_smem_total<C, NP>();
-  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C, NP>,
+  constexpr int smem = s3_smem_total<C, NP, UL>();
+  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C, NP, UL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil3d_kernel<C, NP><<<grid, NT, smem, s>>>(a);
+  stencil3d_kernel<C, NP, UL><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -243,6 +243,12 @@ def autotune_reset():
     N.load().ifcm_autotune_reset()
 
 
+def resident_enable(on=True):
+    """Whole runs of small volumes in one launch (on by default); off sends
+    every batch through the stencil kernels.  See ifcm_resident_enable."""
+    N.load().ifcm_resident_enable(1 if on else 0)
+
+
 def force_plan(np_=0, chunks=1):
     """Make every later launch use np_ particles per item and `chunks`
     z-chunks per tile (np_ = 0 lifts it)."""

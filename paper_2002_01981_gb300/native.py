@@ -122,6 +122,7 @@ SIGNATURES = {
     "ifcm_profile_read": (c_int32, [POINTER(c_double), POINTER(c_int64)]),
     "ifcm_profile_read_kind": (c_int32, [c_int32, POINTER(c_double), POINTER(c_int64)]),
     "ifcm_set_wait_limit_ns": (None, [c_uint64]),
+    "ifcm_resident_enable": (None, [c_int32]),
     "ifcm_fit_noalloc_status": (c_int32, [c_void_p]),
 }
 

@@ -26,6 +26,7 @@ import numpy as np, torch
 from paper_2002_01981_gb300 import build, native
 native.load(build.CHECKED_LIB_PATH)
 from paper_2002_01981_gb300 import ifcm as G, phantoms
+G.resident_enable(False)      # the stencil kernels on every shape
 from oracle import ifcm as O
 from oracle import pso as OP
 
