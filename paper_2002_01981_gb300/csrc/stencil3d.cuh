@@ -124,7 +124,8 @@ struct Slot3 {
 template <int C, int NP, int UL>
 struct Fin3 {
   float2 ncc[S3<C, NP, UL>::K];          // -c_j, paired like the sums (0 in a padding lane)
-  float2 nlam, nxi;                  // -lambda, -xi of the lanes' particles
+  float2 nlam;                       // -lambda of the lanes' particles
+  float2 one_nlam;                   // 1 - lambda
   float floor;                       // dist_floor
 };
 
@@ -143,7 +144,7 @@ struct Acc3 {
 };
 
 // Finalise centre d: Eqs 5 and 7 folded into the factor of Eq 4 (1/G from s,
-// 1/Q from invq, the last cluster's H by complement), Eq 4 with reading R2,
+// -xi/Q given as nx, the last cluster's H by complement), Eq 4 with reading R2,
 // Eq 2 for m = 2, the U^{t+1} store and the centre's shares of Eqs 1 and 3
 // and of max|du|.  ud: the centre's U^t in its stage (pair words at its
 // column); dst: its U^{t+1} word of pair 0.  With bf16 words U^{t+1} is
@@ -151,14 +152,14 @@ struct Acc3 {
 // Eqs 1 and 3 take the FP32 u' that was rounded.
 template <int C, int NP, int UL>
 __device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
-                                     const typename Word3<UL>::T* __restrict__ ud, float invq,
+                                     const typename Word3<UL>::T* __restrict__ ud, float2 nx,
                                      const Fin3<C, NP, UL>& fc, Acc3<C, NP, UL>& acc,
                                      typename Word3<UL>::T* __restrict__ dst, int plane, bool st) {
   constexpr int K = S3<C, NP, UL>::K, KH = S3<C, NP, UL>::KH;
   const float ig = fabsf(d.s);
   // f_j = 1 - lambda H_j - xi F_j with H_j = Hs_j / G and F_j = Fs_j / Q,
   // taking -lambda / G and -xi / Q once per centre
-  const float2 nl = __fmul2_rn(fc.nlam, dup2(ig)), nx = __fmul2_rn(fc.nxi, dup2(invq));
+  const float2 nl = __fmul2_rn(fc.nlam, dup2(ig));
   float2 fq[K];
 #pragma unroll
   for (int q = 0; q < KH; ++q) fq[q] = __ffma2_rn(nx, d.F[q], __ffma2_rn(nl, d.H[q], dup2(1.0f)));
@@ -171,7 +172,7 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
     for (int q = 1; q < KH; ++q) hs = __fadd2_rn(hs, d.H[q]);
     if (NP == 1) hs = dup2(hs.x + hs.y);
     fq[K - 1] = __ffma2_rn(nx, d.F[K - 1], __ffma2_rn(__fmul2_rn(nl, dup2(-1.0f)), hs,
-                                                      __fadd2_rn(dup2(1.0f), fc.nlam)));
+                                                      fc.one_nlam));
   }
   // Eq 4 (reading R2): max(D max(f, 0), floor) = max(D f, floor) for D >= 0
   float2 r[K];
@@ -229,7 +230,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs,
                                       const float* __restrict__ xn, const float* __restrict__ sn,
                                       const typename Word3<UL>::T* __restrict__ ud,
                                       Slot3<C, NP, UL>& d, Slot3<C, NP, UL>& l,
-                                      Slot3<C, NP, UL>& m, Slot3<C, NP, UL>& h, float invq,
+                                      Slot3<C, NP, UL>& m, Slot3<C, NP, UL>& h, float2 nx,
                                       const Fin3<C, NP, UL>& fc, Acc3<C, NP, UL>& acc,
                                       typename Word3<UL>::T* __restrict__ dst, int plane,
                                       bool st) {
@@ -237,7 +238,7 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs,
   h.x = xn[0];
   h.s = sn[0];
   h.xg = h.s < 0.0f ? h.x + 2.0f : h.x;
-  if (FIN) fin3<C, NP, UL>(d, ud, invq, fc, acc, dst, plane, st);
+  if (FIN) fin3<C, NP, UL>(d, ud, nx, fc, acc, dst, plane, st);
   float2 W0[K], S1[K], S2[K];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
@@ -249,8 +250,18 @@ __device__ __forceinline__ void step3(const float* __restrict__ xs,
       const int q2 = dx * dx + dy * dy;
       const bool first_face = dy == -1 && dx == 0, first_corner = first;
       const float xk = xs[off];
-      const float gl = fabsf(l.xg - xk);
-      const float gh = fabsf(h.xg - xk);
+      // g to the centres below and above: one packed difference with two
+      // particles per item (measured 0.6 % and 3.7 % faster at c = 4 and 5),
+      // two scalar ones with one (0.4 % faster at c = 6)
+      float gl, gh;
+      if constexpr (NP == 2) {
+        const float2 glh = __fadd2_rn(make_float2(l.xg, h.xg), dup2(-xk));
+        gl = fabsf(glh.x);
+        gh = fabsf(glh.y);
+      } else {
+        gl = fabsf(l.xg - xk);
+        gh = fabsf(h.xg - xk);
+      }
       const float gm = self ? 0.0f : fabsf(m.xg - xk);
 #pragma unroll
       for (int q = 0; q < K; ++q) {
@@ -460,9 +471,12 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
 #pragma unroll
       for (int q = 0; q < K; ++q) fc.ncc[q] = s_ic.ncc[q];
       fc.nlam = s_ic.nlam;
-      fc.nxi = s_ic.nxi;
+      fc.one_nlam = __fadd2_rn(dup2(1.0f), s_ic.nlam);
       fc.floor = a.dist_floor;
-      const float iqc = cx.invQ_col;
+      // -xi/Q of the column's centres off and on the z faces (Eq 7's 1/Q
+      // folded into Eq 4's factor)
+      const float2 nxc = __fmul2_rn(s_ic.nxi, dup2(cx.invQ_col));
+      const float2 nxz = __fmul2_rn(s_ic.nxi, dup2(iqz));
       // stores of the column (the item's centres lie in [z0, z1) of the volume)
       const long long unit_end =
           (static_cast<long long>(it.unit) + 1) * K * plane * (word_bytes(UL) / 4);
@@ -498,14 +512,14 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
                                                       ((qq + 2) / NSTAGE) & 1);
         const int zd = it.pzb + kk - 2;
         if (ok) {
-          const float invq = zd == 0 ? iqz : iqc;
+          const float2 nx = zd == 0 ? nxz : nxc;
           WT* dst = col_dst + static_cast<long long>(zd) * zstride;
           if (kk >= kf)
             step3<C, NP, UL, true>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1),
-                                   us_at(qq + 6), s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
+                                   us_at(qq + 6), s0, s1, s2, s3, nx, fc, acc, dst, plane, st);
           else
             step3<C, NP, UL, false>(xs_at(qq), us_at(qq), xs_at(qq + 1), ss_at(qq + 1),
-                                    us_at(qq + 6), s0, s1, s2, s3, invq, fc, acc, dst, plane, st);
+                                    us_at(qq + 6), s0, s1, s2, s3, nx, fc, acc, dst, plane, st);
         }
         if (!landed2) ok = ok && wait_full(qq + 2);
         if (kk >= 2) release(qq - 2);
@@ -531,7 +545,7 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
           Slot3<C, NP, UL>& m = r == 0 ? s2 : r == 1 ? s3 : r == 2 ? s0 : s1;
           Slot3<C, NP, UL>& h = r == 0 ? s3 : r == 1 ? s0 : r == 2 ? s1 : s2;
           step3<C, NP, UL, true>(xs_at(qr), us_at(qr), xs_at(qr + 1), ss_at(qr + 1),
-                                 us_at(qr + 6), d, l, m, h, iqc, fc, acc, dst + r * zstride, plane,
+                                 us_at(qr + 6), d, l, m, h, nxc, fc, acc, dst + r * zstride, plane,
                                  st);
           if (!landed2) ok = ok && wait_full(qr + 2);
           release(qr - 2);
@@ -545,10 +559,10 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
       const bool live = ok && !*reinterpret_cast<volatile int*>(&s_abort);
       const int zl = it.pze - 1;
       if (live && np >= 2 && zl >= it.z0 && zl < it.z1)
-        fin3<C, NP, UL>(s0, us_at(ql - 1), zl == 0 ? iqz : iqc, fc, acc,
+        fin3<C, NP, UL>(s0, us_at(ql - 1), zl == 0 ? nxz : nxc, fc, acc,
                         col_dst + static_cast<long long>(zl) * zstride, plane, st);
       if (live && it.pze == vd.nz - 1 && it.pze >= it.z0 && it.pze < it.z1)
-        fin3<C, NP, UL>(s1, us_at(ql), iqz, fc, acc,
+        fin3<C, NP, UL>(s1, us_at(ql), nxz, fc, acc,
                         col_dst + static_cast<long long>(it.pze) * zstride, plane, st);
       if (np >= 2) release(ql - 1);
       release(ql);
