@@ -42,7 +42,9 @@ namespace {
 // volume x with NaN (g = max(|x_i - x_k|, 0) turns it into 0), every other
 // channel with 0.
 constexpr int ATX = 32, ATY = 8, AT = ATX * ATY;
-constexpr int AZ = 8;
+// z-chunks of 32 planes: 8-plane chunks re-read 25 % more halo planes and make
+// 4x the partial records (128^3, K = 20: 9.07 -> 8.00 ms per gradient)
+constexpr int AZ = 32;
 constexpr int HX = ATX + 2, HY = ATY + 2, HP = HX * HY;   // halo plane cells
 
 __device__ __forceinline__ float gdist_nan0(float a, float b) {

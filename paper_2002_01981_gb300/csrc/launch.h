@@ -221,7 +221,7 @@ struct AdjointArgs {
 };
 
 // Blocks (and partial records) of the reverse pass's point kernel: 32 x 8
-// column tiles times z-chunks of 8 planes.
+// column tiles times z-chunks of 32 planes.
 int adjoint_blocks(int nx, int ny, int nz);
 cudaError_t launch_adjoint_point(int c, const AdjointArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_adjoint_gather(int c, const AdjointArgs& a, cudaStream_t s);

@@ -10,6 +10,12 @@ only on U0, so the oracle computes them once.  Then:
 - U^1 of one particle (ifcm_fit) on 20,000 sampled voxels plus every voxel
   of the volume's faces, element by element against the oracle: 1e-5;
 - sum_j u_ij = 1 on every voxel (an invariant at any size).
+
+Those two tests start from a seeded random field, so their one iteration runs
+the general kernel.  The kernel the bench times, the lean 3D kernel, runs every
+iteration whose start comes from Eq 2: a second iteration from the same start
+(two particles, and one particle with U on every voxel), and a whole pifcm3d
+run of one generation from a two-iteration FCM start.
 """
 import numpy as np
 import pytest
@@ -91,3 +97,86 @@ def test_sampled_memberships_of_one_particle(G, case):
         face = (slice(None),) + sl
         assert np.max(np.abs(ug[face] - U1[face])) <= 1e-5
     assert np.max(np.abs(ug.sum(axis=0) - 1.0)) <= 1e-5
+
+
+def test_lean_kernel_two_iterations(G, case):
+    # the kernel the bench times, stencil3d_kernel, at full size in the bench's
+    # plan (two particles per item, whole-column z-chunks): it runs every
+    # iteration whose U^t comes from Eq 2, here the second one.  (lambda, xi)
+    # away from the clamp of reading R2, so that U is compared everywhere.
+    lam_xi = np.array([[0.3, 0.2], [0.45, 0.25]])
+    prm = G.Params(c=C, max_iter=2, eps_u=0.0)
+    G.profile_read(G.PROF_STENCIL3D)
+    G.profile_enable(True)
+    try:
+        G.force_plan(2, 1)
+        try:
+            fit, its, cen = G.pso_fitness_batch(case["x"], prm, lam_xi, case["u0"], case["C0"],
+                                                nx=SHAPE[2], want_centres=True)
+            torch.cuda.synchronize()
+        finally:
+            G.force_plan(0)
+        n3 = G.profile_read(G.PROF_STENCIL3D)[1]
+        Ug, Cg, Jg, _ = G.ifcm_fit(case["x"], prm, tuple(lam_xi[0]), nx=SHAPE[2],
+                                   u_init=case["u0"], c_init=case["C0"])
+        torch.cuda.synchronize()
+        n3_fit = G.profile_read(G.PROF_STENCIL3D)[1]
+    finally:
+        G.profile_enable(False)
+    assert n3 == 1 and n3_fit == 1            # iteration 2 of each call ran the lean kernel
+    assert np.all(its.cpu().numpy() == 2)
+    fit, cen = fit.cpu().numpy(), cen.cpu().numpy()
+    x64 = case["x64"]
+    for p in range(2):
+        lam, xi = lam_xi[p]
+        U1, _, C1 = oracle_step(case, lam, xi)
+        H, F = O.neighbour_terms(x64, U1)
+        d2 = O.modified_distance(x64, C1, H, F, lam, xi)
+        U2 = O.membership(d2, 2.0)
+        J, C2 = O.objective(U2, d2, 2.0), O.centres(x64, U2, 2.0)
+        assert abs(fit[p] - J) <= 1e-5 * abs(J), p
+        assert np.allclose(cen[p], C2, rtol=1e-6, atol=0), p
+        if p == 0:                            # the one-particle form, every voxel
+            ug = Ug[..., :SHAPE[2]].cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(ug - U2)) <= 1e-5
+            assert np.allclose(Cg.cpu().numpy(), C2, rtol=1e-6, atol=0)
+            assert abs(Jg - J) <= 1e-5 * abs(J)
+
+
+def test_lean_kernel_in_a_whole_run(G, case):
+    # what the bench runs: pifcm3d, whose batches start from the FCM start, so
+    # every iteration runs stencil3d_kernel -- two particles per item for the
+    # 20-particle batch, one for the final run.  One generation, one iteration
+    # per fitness, two FCM-start iterations.  The swarm's best lies in the
+    # clamp regime (reading R8), where FP32 and FP64 may put a voxel whose Eq 4
+    # factor is within rounding of 0 on different sides of the clamp, so this
+    # run is checked on its labels, centres and J at the parity suite's bars
+    # for that regime.
+    assert G.stencil_plan(G.shape_of(case["x"], SHAPE[2]), C, P)[:2] == (2, SHAPE[0])
+    raw = phantoms.brain_phantom(SHAPE, seed=2, sigma=0.07)
+    vol = torch.from_numpy(phantoms.pad_pitch(raw)).cuda()
+    prm = G.Params(c=C, max_iter=1, eps_u=0.0)
+    opts = G.Options(P=P, generations=1, seed=2, init_max_iter=2)
+    G.profile_read(G.PROF_STENCIL3D)
+    G.profile_enable(True)
+    try:
+        U, res = G.pifcm3d(vol, prm, opts, nx=SHAPE[2])
+        torch.cuda.synchronize()
+    finally:
+        G.profile_enable(False)
+    assert G.profile_read(G.PROF_STENCIL3D)[1] == 2      # the batch and the final run
+    assert res["status"] == 0 and res["iters_init"] == 2 and res["iters_final"] == 1
+    x64 = case["x64"]
+    U0, C0, _, _ = O.fcm_init(x64, C, 2.0, 2, 0.0)
+    H, F = O.neighbour_terms(x64, U0)
+    lam, xi = res["lambda"], res["xi"]
+    d2 = O.modified_distance(x64, C0, H, F, lam, xi)
+    U1 = O.membership(d2, 2.0)
+    J, C1 = O.objective(U1, d2, 2.0), O.centres(x64, U1, 2.0)
+    ug = U[..., :SHAPE[2]].cpu().numpy().astype(np.float64)
+    assert np.mean(np.argmax(ug, 0) == np.argmax(U1, 0)) >= 0.9999
+    assert np.max(np.abs(ug.sum(axis=0) - 1.0)) <= 1e-5
+    assert np.allclose(res["centres"], C1, rtol=1e-5, atol=0)
+    assert abs(res["J"] - J) <= 1e-4 * abs(J)
+    # the batch's J of the best particle: the same run on the two-particle kernel
+    assert abs(res["best_fitness"] - J) <= 1e-4 * abs(J)
