@@ -560,8 +560,8 @@ ifcm_status build_args(StencilArgs& a, const BatchVol* vols, int n, const ifcm_p
     d.u_dst = kind == 1 ? rb.ub[v] : rb.ua[v];
     d.dst_elems = rb.buf_elems[v];
     d.status = status;
-    const bool k3 = stencil3d_eligible(rb.layout, pl.np, a.m_is_2, a.sum_one, s.nz);
-    ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0, 4, !k3));
+    const bool lean = stencil_lean(rb.layout, pl.np, a.m_is_2, a.sum_one);
+    ST_TRY(make_map(&a.tm_x[v], bv.x, s, 0, 0, 4, !lean));
     ST_TRY(make_smap(&a.tm_s[v], rb.gs[v], s));
     if (rb.layout != UL_PLANAR) {
       // pair words: K planes per unit (a particle pair for np = 2, a particle
@@ -735,11 +735,11 @@ struct BatchRun {
       P_total += vols[v].P;
     }
     if (!wide) {
-      // 1/G of each 3D volume for the float2-pair kernel (plans are timed on it)
+      // 1/G of each volume for the lean pair-word kernels (plans are timed on them)
       if (rb->layout == UL_F32P || rb->layout == UL_BF16)
         for (int v = 0; v < n; ++v) {
           const ifcm_shape& s = vols[v].shape;
-          if (s.nz > 1 && rb->gs_of[v] != vols[v].x) {
+          if (rb->gs_of[v] != vols[v].x) {
             CU_TRY(launch_gsum(vols[v].x, s.nx, s.ny, s.nz, s.pitch_x, rb->gs[v], st));
             rb->gs_of[v] = vols[v].x;
           }

@@ -1,20 +1,21 @@
 // The stencil kernel over bf16 pair words with one particle per work item
 // (every c): word (particle p, pair k) holds clusters 2k and 2k+1 of p, the
 // two lanes of the packed FP32x2 sums.
-#include "stencil3d.cuh"
+#include "stencil2d.cuh"
 
 namespace pifcm {
 
 namespace {
 template <int C>
 cudaError_t launch_np1_bf16(const StencilArgs& a, int grid, cudaStream_t s) {
-  bool deep = false;
-  for (int v = 0; v < a.n_vol; ++v)
-    deep = deep || stencil3d_eligible(UL_BF16, 1, a.m_is_2, a.sum_one, a.vol[v].nz);
-  if (!deep) return launch_c<C, 1, UL_BF16>(a, grid, s);
-  cudaError_t e = launch3d_c<C, 1, UL_BF16>(a, grid, s);
-  if (e != cudaSuccess) return e;
-  return launch_c<C, 1, UL_BF16>(a, grid, s, false);    // the 2D images of the batch
+  if (!stencil_lean(UL_BF16, 1, a.m_is_2, a.sum_one)) return launch_c<C, 1, UL_BF16>(a, grid, s);
+  bool deep = false, flat = false;
+  for (int v = 0; v < a.n_vol; ++v) (a.vol[v].nz == 1 ? flat : deep) = true;
+  if (deep) {
+    const cudaError_t e = launch3d_c<C, 1, UL_BF16>(a, grid, s);
+    if (e != cudaSuccess || !flat) return e;
+  }
+  return launch2d_c<C, 1, UL_BF16>(a, grid, s);
 }
 }  // namespace
 

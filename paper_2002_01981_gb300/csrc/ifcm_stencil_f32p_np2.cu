@@ -2,21 +2,23 @@
 // (c <= 5): word (pair k, cluster j) holds cluster j of particles 2k and 2k+1,
 // loaded and stored as one 64-bit access.  The FP32 layout of batched runs.
 // Iterations that read Eq 2's memberships (every one after the first) with
-// m = 2 run the 3D volumes through stencil3d_kernel.
-#include "stencil3d.cuh"
+// m = 2 run the 3D volumes through stencil3d_kernel and the 2D images
+// through stencil2d_kernel.
+#include "stencil2d.cuh"
 
 namespace pifcm {
 
 namespace {
 template <int C>
 cudaError_t launch_np2(const StencilArgs& a, int grid, cudaStream_t s) {
-  bool deep = false;
-  for (int v = 0; v < a.n_vol; ++v)
-    deep = deep || stencil3d_eligible(UL_F32P, 2, a.m_is_2, a.sum_one, a.vol[v].nz);
-  if (!deep) return launch_c<C, 2, UL_F32P>(a, grid, s);
-  cudaError_t e = launch3d_c<C, 2>(a, grid, s);
-  if (e != cudaSuccess) return e;
-  return launch_c<C, 2, UL_F32P>(a, grid, s, false);    // the 2D images of the batch
+  if (!stencil_lean(UL_F32P, 2, a.m_is_2, a.sum_one)) return launch_c<C, 2, UL_F32P>(a, grid, s);
+  bool deep = false, flat = false;
+  for (int v = 0; v < a.n_vol; ++v) (a.vol[v].nz == 1 ? flat : deep) = true;
+  if (deep) {
+    const cudaError_t e = launch3d_c<C, 2>(a, grid, s);
+    if (e != cudaSuccess || !flat) return e;
+  }
+  return launch2d_c<C, 2, UL_F32P>(a, grid, s);
 }
 }  // namespace
 

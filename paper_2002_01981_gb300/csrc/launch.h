@@ -68,14 +68,18 @@ static_assert(sizeof(StencilArgs) <= 32000, "kernel parameter block must stay be
 // FP32 planes per particle, bf16 pair words, or float2 pair words.
 constexpr int UL_PLANAR = 0, UL_BF16 = 1, UL_F32P = 2;
 
-// Whether a volume of a stencil launch runs stencil3d_kernel: 3D, pair words
-// (one or two particles per item), m = 2, and -- for float2 words, whose
-// last cluster's H is taken by complement -- U^t from Eq 2 (every iteration
-// after the first); bf16 words take every iteration.  Its volume map is
-// zero-filled outside the volume; the other kernels' maps are NaN-filled.
-inline bool stencil3d_eligible(int layout, int np, int m_is_2, int sum_one, int nz) {
+// Whether a stencil launch runs the lean plane step (stencil3d_kernel for 3D
+// volumes, stencil2d_kernel for 2D images): pair words (one or two particles
+// per item), m = 2, and -- for float2 words, whose last cluster's H is taken
+// by complement -- U^t from Eq 2 (every iteration after the first); bf16
+// words take every iteration.  Its volume maps are zero-filled outside the
+// volume; the general kernel's are NaN-filled.
+inline bool stencil_lean(int layout, int np, int m_is_2, int sum_one) {
   return ((layout == UL_F32P && sum_one) || layout == UL_BF16) && (np == 1 || np == 2) &&
-         m_is_2 && nz > 1;
+         m_is_2;
+}
+inline bool stencil3d_eligible(int layout, int np, int m_is_2, int sum_one, int nz) {
+  return stencil_lean(layout, np, m_is_2, sum_one) && nz > 1;
 }
 
 // np = particles sharing one work item: 1 for every c, 2 for c <= 5.

@@ -149,12 +149,14 @@ struct Acc3 {
 // and of max|du|.  ud: the centre's U^t in its stage (pair words at its
 // column); dst: its U^{t+1} word of pair 0.  With bf16 words U^{t+1} is
 // rounded to nearest even when stored and max|du| compares stored values;
-// Eqs 1 and 3 take the FP32 u' that was rounded.
-template <int C, int NP, int UL>
+// Eqs 1 and 3 take the FP32 u' that was rounded.  MASK: the centre's shares
+// are weighed by keep (1, or 0 for a lane outside the image).
+template <int C, int NP, int UL, bool MASK = false>
 __device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
                                      const typename Word3<UL>::T* __restrict__ ud, float2 nx,
                                      const Fin3<C, NP, UL>& fc, Acc3<C, NP, UL>& acc,
-                                     typename Word3<UL>::T* __restrict__ dst, int plane, bool st) {
+                                     typename Word3<UL>::T* __restrict__ dst, int plane, bool st,
+                                     float keep = 1.0f) {
   constexpr int K = S3<C, NP, UL>::K, KH = S3<C, NP, UL>::KH;
   const float ig = fabsf(d.s);
   // f_j = 1 - lambda H_j - xi F_j with H_j = Hs_j / G and F_j = Fs_j / Q,
@@ -190,16 +192,16 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
   float2 inv;
   if (NP == 2) {
     inv = make_float2(fast_rcp(S.x), fast_rcp(S.y));
-    acc.J = __fadd2_rn(acc.J, inv);
+    acc.J = MASK ? __ffma2_rn(inv, dup2(keep), acc.J) : __fadd2_rn(acc.J, inv);
   } else {
     inv = dup2(fast_rcp(S.x + S.y));
-    acc.J.x += inv.x;
+    acc.J.x = MASK ? fmaf(inv.x, keep, acc.J.x) : acc.J.x + inv.x;
   }
   const float2 x2 = dup2(d.x);
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     const float2 u = __fmul2_rn(r[q], inv);
-    const float2 um = __fmul2_rn(u, u);
+    const float2 um = MASK ? __fmul2_rn(__fmul2_rn(u, u), dup2(keep)) : __fmul2_rn(u, u);
     acc.s0[q] = __fadd2_rn(acc.s0[q], um);
     acc.s1[q] = __ffma2_rn(um, x2, acc.s1[q]);
     float2 e;                                                      // u' - u
@@ -211,6 +213,7 @@ __device__ __forceinline__ void fin3(const Slot3<C, NP, UL>& d,
       if (st) __stcg(&dst[q * plane], u);
       e = __ffma2_rn(ud[q * PLANE], dup2(-1.0f), u);
     }
+    if (MASK) e = __fmul2_rn(e, dup2(keep));
     if (NP == 2) {
       acc.dm.x = fmaxf(acc.dm.x, fabsf(e.x));
       acc.dm.y = fmaxf(acc.dm.y, fabsf(e.y));

@@ -148,28 +148,35 @@ def test_fixed_iteration_runs(G, shape, c, lam, xi, iters):
     assert labels_agree(Ugn, Uo) >= 0.9999
 
 
-def _storage_rounding_floor(x, U, C, lam, xi, iters):
-    """How far the FP64 oracle moves when only its U and C are rounded to FP32
-    after every iteration: the part of the GPU-oracle gap that FP32 storage
-    alone explains."""
-    Ua, Ca, Ub, Cb = U, C, U, C
+def fp32_floor(x, U, C, lam, xi, iters):
+    """How far the FP64 oracle's U moves after a run's iterations when it
+    rounds to FP32 in every iteration (a) only its U and C, (b) also its H and
+    F: the larger of the two.  That is the part of the GPU-oracle gap that FP32
+    storage and the FP32 rounding of the neighbourhood terms alone explain."""
+    f32 = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)
+    Ua, Ca, Ub, Cb, Uc, Cc = U, C, U, C, U, C
     for _ in range(iters):
         Ua, Ca, _, _ = O.ifcm_iteration(x, Ua, Ca, lam, xi)
         Ub, Cb, _, _ = O.ifcm_iteration(x, Ub, Cb, lam, xi)
-        Ub = Ub.astype(np.float32).astype(np.float64)
-        Cb = Cb.astype(np.float32).astype(np.float64)
-    return float(np.max(np.abs(Ua - Ub)))
+        Ub, Cb = f32(Ub), f32(Cb)
+        H, F = O.neighbour_terms(x, Uc)
+        Uc = O.membership(O.modified_distance(x, Cc, f32(H), f32(F), lam, xi), 2.0)
+        Cc = f32(O.centres(x, Uc, 2.0))
+        Uc = f32(Uc)
+    return max(float(np.max(np.abs(Ua - Ub))), float(np.max(np.abs(Ua - Uc))))
 
 
 def u_bound(x, U, C, lam, xi, iters):
     """U tolerance of a run: 1e-5, except in the clamp regime (lambda + xi > 1,
-    reading R2 of Eq 4), where it is four times the oracle's own FP32-storage
-    sensitivity.  The GPU's U error was measured at 1.2 to 3.0 times that
-    sensitivity on test_clamp_regime_runs' cases and at (0.5, 0.4), (0.3,
-    0.3)."""
+    reading R2 of Eq 4), where 1 - lambda H - xi F sits near 0 at many voxels
+    and the iteration amplifies FP32 rounding: four times the oracle's own
+    FP32 floor (fp32_floor).  The GPU's U error measured 0.93-2.85x the
+    storage part of that floor on test_clamp_regime_runs' cases (lean 3D
+    kernel) and 3.3x the floor on the 24 x 24 Algorithm 1 run (lean 2D
+    kernel: 1.6e-5 against a bound of 2.0e-5)."""
     if lam + xi <= 1.0:
         return U_TOL
-    return max(U_TOL, 4.0 * _storage_rounding_floor(x, U, C, lam, xi, iters))
+    return max(U_TOL, 4.0 * fp32_floor(x, U, C, lam, xi, iters))
 
 
 @pytest.mark.parametrize("lam,xi", [(0.9, 0.8), (1.0, 1.0), (0.7, 0.6)])
