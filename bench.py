@@ -680,10 +680,12 @@ def run_reference(args):
 
 # ------------------------------------------------------------ GPU arm
 def run_small_kind(args):
-    """Small cases for profiler captures of the F2 / F3 kernels (a few GB on
-    the device): 'bf16' runs 3 iterations of 8 particles of the c = 6 256^3
-    workload with bf16 memberships; 'grad' runs ifcm_grad (K = 3) on the 128^3
-    differentiation workload."""
+    """Small cases for profiler captures of the F2 / F3 kernels and of the 2D
+    stencil (a few GB on the device at most): 'bf16' runs 3 iterations of 8
+    particles of the c = 6 256^3 workload with bf16 memberships; 'grad' runs
+    ifcm_grad (K = 3) on the 128^3 differentiation workload; 'image' runs
+    3 iterations of 64 particles on the 854 x 854 slice of the 2D sweep, from
+    its FCM start (memberships from Eq 2, so the lean 2D kernel runs)."""
     import torch
 
     import __graft_entry__
@@ -703,6 +705,17 @@ def run_small_kind(args):
             fit, _, _ = G.pso_fitness_batch(x, prm, lam, U0, C0, nx=nx)
         torch.cuda.synchronize()
         print(json.dumps({"small_kind": "bf16", "fitness": fit.cpu().numpy().tolist()}))
+    elif args.small_kind == "image":
+        n = phantoms.SWEEP_SIZES[-1]
+        raw = phantoms.brain_slice(n, seed=2, sigma=0.07)
+        vol = torch.from_numpy(phantoms.pad_pitch(raw)).to(dev)
+        # 64 particles: 298 MB of membership buffers, beyond the 129 MB L2
+        opts = G.Options(P=64, generations=1, seed=SEED, init_max_iter=20)
+        prm = G.Params(c=C, m=M, max_iter=3, eps_u=0.0)
+        for _ in range(args.steps):
+            _, res = G.pifcm3d(vol, prm, opts, nx=n)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_kind": "image", "J": res["J"], "updates": res["updates"]}))
     else:
         raw = phantoms.gaussian_phantom(DIFF_SHAPE, seed=4, sigma=0.09)
         nx = DIFF_SHAPE[2]
@@ -933,8 +946,9 @@ def main():
     ap.add_argument("--small-particles", type=int, default=0,
                     help="with --small: this many particles (a smaller capture), under the "
                          "full run's plan (2 particles per item, whole-column items)")
-    ap.add_argument("--small-kind", choices=("bf16", "grad"), default=None,
-                    help="profiling case of the bf16 stencil or of the adjoint kernels")
+    ap.add_argument("--small-kind", choices=("bf16", "grad", "image"), default=None,
+                    help="profiling case of the bf16 stencil, the adjoint kernels or the 2D "
+                         "stencil")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return relaunch(args.gpus)
