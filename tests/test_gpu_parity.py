@@ -544,6 +544,45 @@ def test_2d_runs_of_tiles_match_oracle(G, chunks):
     assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
 
 
+@pytest.mark.parametrize("c,P", [(4, 4), (3, 3), (6, 2)])
+def test_lean_2d_kernel_on_the_largest_sweep_slice(G, c, P):
+    # the 854 x 854 slice of the 2D sweep: iteration 1 from a shared random
+    # start runs the general kernel, iteration 2 (U^t from Eq 2) the lean 2D
+    # kernel -- two particles per item for c <= 5, one for c = 6.  J, C of
+    # every particle against the oracle, and U of one particle (ifcm_fit, the
+    # one-particle form) on every pixel
+    n = 854
+    raw = phantoms.brain_slice(n, seed=2, sigma=0.07)
+    x = O.normalize(raw).astype(np.float32)
+    U0 = phantoms.random_memberships(x.shape, c, seed=151)
+    C0 = np.linspace(0.1, 0.9, c)
+    lam_xi = np.random.default_rng(152).random((P, 2)) * 0.5
+    prm = G.Params(c=c, max_iter=2, eps_u=0.0)
+    G.profile_read(G.PROF_STENCIL)
+    G.profile_enable(True)
+    try:
+        fit, its, cen = G.pso_fitness_batch(dev_vol(x), prm, lam_xi, dev_u(U0), C0, nx=n,
+                                            want_centres=True)
+        Ug, Cg, Jg, _ = G.ifcm_fit(dev_vol(x), prm, tuple(lam_xi[0]), nx=n, u_init=dev_u(U0),
+                                   c_init=C0)
+        torch.cuda.synchronize()
+    finally:
+        G.profile_enable(False)
+    assert G.profile_read(G.PROF_STENCIL)[1] == 4           # two launches per call
+    assert np.all(its.cpu().numpy() == 2)
+    fit, cen = fit.cpu().numpy(), cen.cpu().numpy()
+    x64 = x.astype(np.float64)
+    for p in range(P):
+        Uo, Co, Jo, _ = O.ifcm_fit(x64, U0.astype(np.float64), C0, lam_xi[p, 0], lam_xi[p, 1],
+                                   2.0, 2, 0.0)
+        assert abs(fit[p] - Jo) <= J_RTOL * abs(Jo), p
+        assert np.allclose(cen[p], Co, rtol=C_RTOL, atol=0), p
+        if p == 0:
+            assert np.max(np.abs(unpad(Ug, n) - Uo)) <= U_TOL
+            assert np.allclose(Cg.cpu().numpy(), Co, rtol=C_RTOL)
+            assert abs(Jg - Jo) <= J_RTOL * abs(Jo)
+
+
 def test_autotuned_plan_is_cached_and_matches_oracle(G):
     shape = (24, 40, 70)
     x = unit_volume(shape, seed=131)
