@@ -313,3 +313,38 @@ def test_graph_capture_of_a_resident_run(G):
     assert r1["lambda"] == r2["lambda"] and r1["xi"] == r2["xi"]
     assert r1["J"] == r2["J"] and r1["iters_final"] == r2["iters_final"]
     assert torch.equal(U1, U2)
+
+
+def test_slice_mode_runs_resident(G):
+    # Algorithm 1 step 1 (one slice of a volume): the slice fits a CTA's shared
+    # memory, so its FCM start and fitness batches run resident
+    raw = phantoms.brain_phantom((6, 20, 22), seed=8)
+    prm = G.Params(c=3, max_iter=5, eps_u=0.0)
+    opts = G.Options(P=3, generations=2, seed=4, init_max_iter=30, slice_z=2)
+    (U, res), n_st = stencil_launches(G, lambda: G.pifcm3d(dev_vol(raw), prm, opts, nx=22))
+    assert n_st == 0
+    ref = OP.pifcm3d(raw, c=3, P=3, generations=2, seed=4, max_iter=5, eps=0.0,
+                     init_max_iter=30, z=2)
+    assert U.shape[1] == 1
+    assert res["lambda"] == ref["lambda"] and res["xi"] == ref["xi"]
+    x = O.normalize(raw)[2:3]
+    U0, C0, _, _ = O.fcm_init(x, 3, 2.0, 30, 0.0)
+    bound = u_bound(x, U0, C0, ref["lambda"], ref["xi"], 5)
+    assert np.max(np.abs(unpad(U, 22) - ref["U"])) <= bound
+    assert np.allclose(res["centres"], ref["C"], rtol=1e-5)
+    assert abs(res["J"] - ref["J"]) <= 1e-4 * abs(ref["J"])
+
+
+def test_bf16_batches_keep_the_stencil_kernels(G):
+    # resident runs hold FP32 memberships only: a bf16 batch of a small volume
+    # runs the stencil kernels and stores bf16
+    shape = (4, 9, 11)
+    x = unit_volume(shape, seed=91)
+    U0 = phantoms.random_memberships(shape, 4, seed=92)
+    C0 = np.array([0.1, 0.35, 0.6, 0.85])
+    lam_xi = np.array([[0.3, 0.2], [0.4, 0.1]])
+    prm = G.Params(c=4, max_iter=3, eps_u=0.0, u_dtype="bf16")
+    (fit, its, _), n_st = stencil_launches(
+        G, lambda: G.pso_fitness_batch(dev_vol(x), prm, lam_xi, dev_u(U0), C0, nx=11))
+    assert n_st == 3
+    assert np.all(its.cpu().numpy() == 3)
