@@ -311,6 +311,24 @@ def test_pifcm3d_ellipse_slice_full_workload(G):
     assert labels_agree(unpad(U, 64), Uo) >= 0.999
     assert np.allclose(res["centres"], Co, rtol=1e-4, atol=0)
     assert abs(res["J"] - Jo) <= 1e-4 * abs(Jo)
+    # The same final run replayed by the oracle from the GPU's own normalised
+    # volume and FCM start (the same resident launch as pifcm3d's, from
+    # u = 1/c and c_j = (j + 1/2)/c), for the GPU's iteration count.  Only
+    # FP32 rounding separates the two, so the parity bars apply: U within the
+    # clamp-regime conditioning bound (u_bound), labels, C and J.
+    xg = G.ifcm_normalize(dev_vol(raw), nx=64)
+    U0g, C0g, _, it0g = G.ifcm_fit(xg, G.Params(c=4, max_iter=300, eps_u=1e-5), (0.0, 0.0),
+                                   nx=64)
+    assert it0g == res["iters_init"]
+    xs = xg.cpu().numpy()[..., :64].astype(np.float64)
+    U0s = unpad(U0g, 64).astype(np.float64)
+    C0s = C0g.cpu().numpy().astype(np.float64)
+    lam, xi, its = res["lambda"], res["xi"], res["iters_final"]
+    Ur, Cr, Jr, _ = O.ifcm_fit(xs, U0s, C0s, lam, xi, 2.0, its, 0.0)
+    assert np.max(np.abs(unpad(U, 64) - Ur)) <= u_bound(xs, U0s, C0s, lam, xi, its)
+    assert labels_agree(unpad(U, 64), Ur) >= 0.9999
+    assert np.allclose(res["centres"], Cr, rtol=1e-5, atol=0)
+    assert abs(res["J"] - Jr) <= J_RTOL * abs(Jr)
 
 
 def test_pifcm3d_small_run_matches_oracle(G):
