@@ -149,9 +149,10 @@ def test_lean_kernel_in_a_whole_run(G, case):
     # 20-particle batch, one for the final run.  One generation, one iteration
     # per fitness, two FCM-start iterations.  The swarm's best lies in the
     # clamp regime (reading R8), where FP32 and FP64 may put a voxel whose Eq 4
-    # factor is within rounding of 0 on different sides of the clamp, so this
-    # run is checked on its labels, centres and J at the parity suite's bars
-    # for that regime.
+    # factor is within rounding of 0 on different sides of the clamp: U is
+    # held to 1e-5 on 99.99 % of the voxels (measured: the 99.99th percentile
+    # 2.0e-6, the largest 4.2e-4), labels, centres and J to the parity bars
+    # (measured: labels all equal, C 2.6e-8, J 1.3e-7).
     assert G.stencil_plan(G.shape_of(case["x"], SHAPE[2]), C, P)[:2] == (2, SHAPE[0])
     raw = phantoms.brain_phantom(SHAPE, seed=2, sigma=0.07)
     vol = torch.from_numpy(phantoms.pad_pitch(raw)).cuda()
@@ -175,8 +176,9 @@ def test_lean_kernel_in_a_whole_run(G, case):
     J, C1 = O.objective(U1, d2, 2.0), O.centres(x64, U1, 2.0)
     ug = U[..., :SHAPE[2]].cpu().numpy().astype(np.float64)
     assert np.mean(np.argmax(ug, 0) == np.argmax(U1, 0)) >= 0.9999
+    assert np.mean(np.abs(ug - U1) <= 1e-5) >= 0.9999
     assert np.max(np.abs(ug.sum(axis=0) - 1.0)) <= 1e-5
-    assert np.allclose(res["centres"], C1, rtol=1e-5, atol=0)
-    assert abs(res["J"] - J) <= 1e-4 * abs(J)
+    assert np.allclose(res["centres"], C1, rtol=1e-6, atol=0)
+    assert abs(res["J"] - J) <= 1e-5 * abs(J)
     # the batch's J of the best particle: the same run on the two-particle kernel
-    assert abs(res["best_fitness"] - J) <= 1e-4 * abs(J)
+    assert abs(res["best_fitness"] - J) <= 1e-5 * abs(J)
