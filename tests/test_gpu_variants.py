@@ -120,12 +120,12 @@ def test_pifcm3d_with_shells(G):
                      init_max_iter=30, V=2, h=1.0)
     assert res["status"] == 0
     assert res["lambda"] == ref["lambda"] and res["xi"] == ref["xi"]
-    x = O.normalize(raw)
-    U0, C0, _, _ = O.fcm_init(x, 3, 2.0, 30, 0.0)
-    bound = u_bound(x, U0, C0, ref["lambda"], ref["xi"], 4) if ref["lambda"] + ref["xi"] <= 1 \
-        else 1e-3
-    assert np.max(np.abs(unpad(U, 16) - ref["U"])) <= max(bound, U_TOL)
-    assert abs(res["J"] - ref["J"]) <= 1e-4 * abs(ref["J"])
+    # the swarm ends at (1, 0.51), in the clamp regime; measured on a GB300
+    # (stencil and resident forms): U 5.9e-6, labels all equal, C 4.8e-8, J 4.0e-7
+    assert np.max(np.abs(unpad(U, 16) - ref["U"])) <= U_TOL
+    assert labels_agree(unpad(U, 16), ref["U"]) >= 0.9999
+    assert np.allclose(res["centres"], ref["C"], rtol=C_RTOL)
+    assert abs(res["J"] - ref["J"]) <= J_RTOL * abs(ref["J"])
 
 
 def j_bound(ref, nvox, dist_floor=1e-12):
