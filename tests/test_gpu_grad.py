@@ -1,8 +1,8 @@
 """dJ^{K-1}/d(lambda, xi) on the GPU (C ABI: ifcm_grad, ifcm_polish) against
 the FP64 oracle adjoint, and the autograd wrapper.
 
-Tolerance: 1e-4 relative on each derivative (FP32 forward and reverse passes
-against FP64, K up to 20), 1e-5 relative on J.  Starts are seeded random
+Tolerance: 1e-5 relative on each derivative and on J (FP32 forward and reverse
+passes against FP64, K up to 20; measured on a GB300 within 5.8e-7 and 1.7e-7).  Starts are seeded random
 memberships from the shared input generator, so both sides begin from the
 same (U^0, C^0).  Points are chosen with 1 - lambda H - xi F > 0 almost
 everywhere (lambda + xi < 1), away from the clamp of reading R2 whose kink
@@ -19,7 +19,7 @@ from paper_2002_01981_gb300 import phantoms      # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-G_RTOL = 1e-4
+G_RTOL = 1e-5
 J_RTOL = 1e-5
 
 
