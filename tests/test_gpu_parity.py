@@ -443,13 +443,14 @@ MULTI_SPECS = [((9, 14, 21), 3, 3), ((16, 12, 33), 4, 5), ((5, 30, 17), 3, 1),
                ((12, 12, 12), 6, 4), ((20, 9, 40), 4, 2), ((1, 40, 37), 4, 3)]
 
 
-def _multi_inputs(G, specs, seed):
+def _multi_inputs(G, specs, seed, scale=1.0):
+    # scale <= 0.5 keeps lambda + xi <= 1, out of the clamp regime
     vols, host = [], []
     for k, (shape, c, P) in enumerate(specs):
         x = unit_volume(shape, seed=seed + k)
         U0 = phantoms.random_memberships(shape, c, seed=seed + 100 + k)
         C0 = np.sort(np.random.default_rng(seed + 200 + k).random(c))
-        lam_xi = np.random.default_rng(seed + 300 + k).random((P, 2))
+        lam_xi = np.random.default_rng(seed + 300 + k).random((P, 2)) * scale
         vols.append(G.BatchVolume(dev_vol(x), c, lam_xi, dev_u(U0), C0, nx=shape[2]))
         host.append((x, U0, C0, lam_xi))
     return vols, host
@@ -473,6 +474,47 @@ def test_fitness_multi_matches_oracle(G):
     for (x, U0, C0, lam_xi), (fit, its) in zip(host, outs):
         fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
                                   max_iter=8, eps=0.0)
+        assert np.array_equal(its.cpu().numpy(), io)
+        assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
+
+
+def test_fitness_batch_at_the_particle_limit(G):
+    # the most particles one batch takes (1024): every particle's J and C
+    # against the oracle (lambda + xi <= 1, out of the clamp regime, where the
+    # parity bars apply); one more is rejected before anything is launched
+    from paper_2002_01981_gb300.native import IfcmError
+    shape, c, P = (3, 4, 5), 3, 1024
+    x = unit_volume(shape, seed=41)
+    U0 = phantoms.random_memberships(shape, c, seed=42)
+    C0 = np.array([0.2, 0.5, 0.8])
+    lam_xi = np.random.default_rng(43).random((P, 2)) * 0.5
+    prm = G.Params(c=c, max_iter=3, eps_u=0.0)
+    fit, its, cen = G.pso_fitness_batch(dev_vol(x), prm, lam_xi, dev_u(U0), C0, nx=shape[2],
+                                        want_centres=True)
+    fit, its, cen = fit.cpu().numpy(), its.cpu().numpy(), cen.cpu().numpy()
+    assert np.all(its == 3)
+    x64, U64 = x.astype(np.float64), U0.astype(np.float64)
+    for p in range(P):
+        _, Co, Jo, _ = O.ifcm_fit(x64, U64, C0, lam_xi[p, 0], lam_xi[p, 1], 2.0, 3, 0.0)
+        assert abs(fit[p] - Jo) <= J_RTOL * abs(Jo), p
+        assert np.allclose(cen[p], Co, rtol=C_RTOL), p
+    with pytest.raises(IfcmError):
+        G.pso_fitness_batch(dev_vol(x), prm, np.full((P + 1, 2), 0.5), dev_u(U0), C0,
+                            nx=shape[2])
+
+
+def test_fitness_multi_at_the_launch_limits(G):
+    # 70 volumes of 64 particles: the first wave fills one launch's 64 volumes
+    # and 4096 particles at once, the second takes the other 6 volumes
+    specs = [((2 + k % 3, 3 + k % 4, 4 + k % 5), 3, 64) for k in range(70)]
+    vols, host = _multi_inputs(G, specs, seed=91, scale=0.5)
+    prm = G.Params(max_iter=3, eps_u=0.0)
+    ws_bytes = G.pso_fitness_multi_workspace_bytes(vols, prm)
+    assert G.pso_fitness_multi_waves(vols, prm, ws_bytes) == 2
+    outs = G.pso_fitness_multi(vols, prm)
+    for (x, U0, C0, lam_xi), (fit, its) in zip(host, outs):
+        fo, io = OP.fitness_batch(x.astype(np.float64), U0.astype(np.float64), C0, lam_xi,
+                                  max_iter=3, eps=0.0)
         assert np.array_equal(its.cpu().numpy(), io)
         assert np.all(np.abs(fit.cpu().numpy() - fo) <= J_RTOL * np.abs(fo))
 
