@@ -131,25 +131,42 @@ __global__ void __launch_bounds__(RT3, 1) resident_kernel(const __grid_constant_
       if (stencil) {
         float G = 0.0f, Q = 0.0f;
         int cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              if (dx == 0 && dy == 0 && dz == 0) continue;
-              const int kx = X + dx, ky = Y + dy, kz = Z + dz;
-              if (kx < 0 || kx >= nx || ky < 0 || ky >= ny || kz < 0 || kz >= nz) continue;
-              const int kk = (kz * ny + ky) * nx + kx;
-              const float g = fabsf(xc - sx[kk]);                                // Eq 6
-              const float q2 = static_cast<float>(dx * dx + dy * dy + dz * dz);  // Eq 8
+        // neighbour kk at squared distance q2 (Eqs 6 and 8); u_k^2 is
+        // rounded before the q2 term (__fmul_rn is never contracted), so a
+        // constant q2 gives the sums of a variable one
+        auto add = [&](int kk, float q2) {
+          const float g = fabsf(xc - sx[kk]);
 #pragma unroll
-              for (int j = 0; j < C; ++j) {
-                const float uk = su[j * N + kk];
-                H[j] = fmaf(uk, g, H[j]);
-                F[j] = fmaf(uk * uk, q2, F[j]);
-              }
-              G += g;
-              Q += q2;
-              ++cnt;
+          for (int j = 0; j < C; ++j) {
+            const float uk = su[j * N + kk];
+            H[j] = fmaf(uk, g, H[j]);
+            F[j] = fmaf(__fmul_rn(uk, uk), q2, F[j]);
+          }
+          G += g;
+          Q += q2;
+          ++cnt;
+        };
+        if (nz == 1) {
+          // an image: the 8 in-plane neighbours, in the order of the 3D loop
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dx == 0 && dy == 0) continue;
+              const int kx = X + dx, ky = Y + dy;
+              if (kx < 0 || kx >= nx || ky < 0 || ky >= ny) continue;
+              add(ky * nx + kx, static_cast<float>(dx * dx + dy * dy));
             }
+        } else {
+          for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const int kx = X + dx, ky = Y + dy, kz = Z + dz;
+                if (kx < 0 || kx >= nx || ky < 0 || ky >= ny || kz < 0 || kz >= nz) continue;
+                add((kz * ny + ky) * nx + kx, static_cast<float>(dx * dx + dy * dy + dz * dz));
+              }
+        }
         if (cnt > 0) {
           const float invQ = __frcp_rn(Q);
 #pragma unroll
