@@ -9,9 +9,47 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/pifcm.h"
 
 namespace pifcm {
+
+// Programmatic dependent launch.  A kernel launched by launch_dependent() may
+// be scheduled while the kernel before it on the stream is still running; it
+// calls grid_dep_wait() before its first access to memory, which returns once
+// that kernel has completed and its writes are visible.  grid_dep_trigger()
+// lets the next such kernel be scheduled; it takes effect once every CTA of
+// the grid has called it or exited, so the grids before it are all resident.
+// A stream being captured into a CUDA graph gets ordinary launches: the graph
+// already hides the launch latency, and programmatic edges there measured
+// slower (whole 165^2 and 285^2 runs 4-6 %), where direct launches gain
+// 6-23 %.  Without a programmatic dependency grid_dep_wait() returns at once.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... K, typename... A>
+cudaError_t launch_dependent(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
+  cfg.attrs = at;
+  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr int kMaxC = 8;            // clusters supported by the kernels
 constexpr int kMaxP = 1024;         // particles per swarm / batch

@@ -284,6 +284,9 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const ReduceArgs a) {
   __shared__ double s_sum[NV][RT];
   __shared__ float s_max[RT];
   const int gp = blockIdx.x;                 // particle of the launch
+  // launched as a dependent of the stencil launch before it
+  grid_dep_trigger();
+  grid_dep_wait();
   if (!a.st.active[gp]) return;
   int vi = 0;
   while (vi + 1 < a.n_vol && a.vol[vi + 1].pbase <= gp) ++vi;
@@ -395,7 +398,7 @@ cudaError_t launch_plain(int c, const PlainArgs& a, const ShellArgs& sh, int blo
 }
 
 cudaError_t launch_reduce(int c, const ReduceArgs& a, cudaStream_t s) {
-  PIFCM_DISPATCH_C(c, (reduce_kernel<C><<<a.P_total, RT, 0, s>>>(a)); return cudaGetLastError());
+  PIFCM_DISPATCH_C(c, return launch_dependent(reduce_kernel<C>, dim3(a.P_total), dim3(RT), 0, s, a));
 }
 
 cudaError_t launch_run_init(int c, int P, const double* c0, RunState st, double* J_clear,

@@ -80,6 +80,10 @@ __global__ void __launch_bounds__(NT, 1) stencil2d_kernel(const __grid_constant_
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
   __shared__ ItemConst<C, NP> s_ic;
+  // launched as a dependent of the stream's previous kernel: let the next
+  // kernel be scheduled, and touch no memory before this one has finished
+  grid_dep_trigger();
+  grid_dep_wait();
 
   unsigned char* dsmem = dsmem_raw + ((128u - (smem_addr(dsmem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x;
@@ -366,8 +370,7 @@ cudaError_t launch2d_c(const StencilArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(stencil2d_kernel<C, NP, UL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil2d_kernel<C, NP, UL><<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(stencil2d_kernel<C, NP, UL>, dim3(grid), dim3(NT), smem, s, a);
 }
 
 }  // namespace

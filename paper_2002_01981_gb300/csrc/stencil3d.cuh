@@ -302,6 +302,10 @@ __global__ void __launch_bounds__(NT, 1) stencil3d_kernel(const __grid_constant_
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
   __shared__ ItemConst<C, NP> s_ic;
+  // launched as a dependent of the stream's previous kernel: let the next
+  // kernel be scheduled, and touch no memory before this one has finished
+  grid_dep_trigger();
+  grid_dep_wait();
 
   // 128-byte aligned start by pointer arithmetic, so that the compiler keeps
   // the shared address space of every stage pointer
@@ -644,8 +648,7 @@ cudaError_t launch3d_c(const StencilArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<C, NP, UL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  stencil3d_kernel<C, NP, UL><<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(stencil3d_kernel<C, NP, UL>, dim3(grid), dim3(NT), smem, s, a);
 }
 
 }  // namespace

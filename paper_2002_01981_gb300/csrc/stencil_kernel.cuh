@@ -649,6 +649,10 @@ __global__ void __launch_bounds__(NT, PIFCM_STENCIL_MIN_BLOCKS)
   __shared__ int s_abort;
   __shared__ float s_red[NCW][NP * (2 * C + 2)];
   __shared__ ItemConst<C, NP> s_ic;
+  // launched as a dependent of the stream's previous kernel: let the next
+  // kernel be scheduled, and touch no memory before this one has finished
+  grid_dep_trigger();
+  grid_dep_wait();
 
   unsigned char* dsmem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -1046,16 +1050,14 @@ cudaError_t launch_c(const StencilArgs& a, int grid, cudaStream_t s, bool deep_o
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    stencil_kernel<C, NP, UL, false><<<grid, NT, smem, s>>>(a);
-    e = cudaGetLastError();
+    e = launch_dependent(stencil_kernel<C, NP, UL, false>, dim3(grid), dim3(NT), smem, s, a);
     if (e != cudaSuccess) return e;
   }
   if (flat) {
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel<C, NP, UL, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    stencil_kernel<C, NP, UL, true><<<grid, NT, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(stencil_kernel<C, NP, UL, true>, dim3(grid), dim3(NT), smem, s, a);
   }
   return cudaSuccess;
 }
